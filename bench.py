@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the fused D3Q27 collide-and-stream step (MLUPS, % of HBM
+roofline) on one GB300, with the FP64 oracle as the CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One bench step is one lattice time step of the D3Q27 Taylor-Green + noise
+workload (256^3 periodic, tau = 0.6, FP32 storage): one launch of the fused
+step kernel.  Inputs are larger than L2 (two 1.8 GB state buffers), so no L2
+flush is needed between steps.  With N > 1 (torchrun) every rank runs the
+same workload on its own GPU (independent replicas: the method is not
+sharded across GPUs here) and the slowest rank's time counts.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q27 fused step MLUPS and % of HBM roofline; adjoint/forward step-time ratio"
+UNIT = "MLUPS"
+BYTES_PER_CELL = {("q27", "f32"): 216, ("q27", "f16"): 108, ("q27", "bf16"): 108,
+                  ("q15", "f32"): 120}
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["lattice.cuh", "collide_q27.cuh", "kernels.cuh", "kernels_q27.cu"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--size", type=int, default=256, help="cube edge of the main workload")
+    p.add_argument("--quick", action="store_true",
+                   help="main measurement only (no e2e, sweeps, 16-bit or CPU baseline)")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for n in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1202_6081_gb300", "csrc", n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(size):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, scaled to the workload's cells; None if the kernel changed."""
+    path = os.path.join(ROOT, "profiles", "step_q27_f32_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d["dram_bytes_per_cell"] * size**3
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(size, budget_s=15.0):
+    """The FP64 oracle on this host's cores, on a bounded sample of the same
+    workload: z-slabs of the size^3 Taylor-Green + noise field (periodic),
+    stepped until about budget_s of CPU work has run."""
+    import oracle
+    import workloads as W
+    oracle.build()
+    Q = 27
+    om = W.omegas(Q, 1 / 0.6)
+    nz_s = 1
+    shape = (nz_s, size, size)
+    rho, u = W.taylor_green((size, size, size), u0=0.02, noise=1e-3)
+    f = oracle.equilibrium(Q, rho[:nz_s], u[:, :nz_s], np.zeros(3))
+    t0 = time.perf_counter()
+    oracle.run(Q, shape, f, np.zeros(3), om, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    oracle.run(Q, shape, f, np.zeros(3), om, steps)
+    dt = time.perf_counter() - t0
+    cells = size * size * nz_s
+    return {"value": cells * steps / dt / 1e6, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": "%d steps of one %dx%dx%d z-slab of the %d^3 Taylor-Green+noise field "
+                      "(periodic), D3Q27, tau=0.6, FP64, %.1f s" % (steps, size, size, nz_s,
+                                                                   size, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import workloads as W
+    oracle.build()
+    Q = 27
+    size = args.size
+    om = W.omegas(Q, 1 / 0.6)
+    rho, u = W.taylor_green((size, size, size), u0=0.02, noise=1e-3)
+    # each reference step: one oracle step on a z-slab of the workload, the
+    # slab sized so that warmup + steps end within about two minutes
+    probe = (1, size, size)
+    f1 = oracle.equilibrium(Q, rho[:1], u[:, :1], np.zeros(3))
+    t0 = time.perf_counter()
+    oracle.run(Q, probe, f1, np.zeros(3), om, 1)
+    per_plane = time.perf_counter() - t0
+    total_steps = args.steps + args.warmup
+    budget = 120.0
+    planes = max(1, min(size, int(budget / max(total_steps * per_plane, 1e-9))))
+    cells_side = size
+    if planes == 1 and total_steps * per_plane > budget:
+        # shrink the slab's rows too
+        frac = budget / (total_steps * per_plane)
+        cells_side = max(8, int(size * frac))
+    shape = (planes, cells_side, size)
+    f = oracle.equilibrium(Q, rho[:planes, :cells_side], u[:, :planes, :cells_side],
+                           np.zeros(3))
+    for _ in range(args.warmup):
+        f = oracle.run(Q, shape, f, np.zeros(3), om, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.run(Q, shape, f, np.zeros(3), om, 1)
+    dt = time.perf_counter() - t0
+    cells = planes * cells_side * size
+    value = cells * args.steps / dt / 1e6
+    sample = ("each step: one oracle step on a %dx%dx%d slab of the %d^3 Taylor-Green+noise "
+              "field (periodic), D3Q27, tau=0.6, FP64" % (size, cells_side, planes, size))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "D3Q27 Taylor-Green+noise %d^3 periodic, tau=0.6" % size,
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def make_solver(lbm, Q, size, storage, tau):
+    import workloads as W
+    shape = (size, size, size)
+    om = W.omegas(Q, 1 / tau)
+    rho, u = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    S = lbm.Solver(Q, shape, om, storage=storage)
+    S.init_equilibrium(rho, u)
+    return S, rho, u
+
+
+def time_steps(torch, S, steps, warmup, barrier=None):
+    stream = torch.cuda.current_stream()
+    S.step(warmup)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    S.step(steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    return start.elapsed_time(end) / 1e3
+
+
+def e2e_job(torch, lbm, size, steps):
+    """Whole job through the public API from pinned host buffers: upload
+    rho, u (FP64), initialise, `steps` steps, download rho, u (FP32)."""
+    import workloads as W
+    Q = 27
+    shape = (size, size, size)
+    N = size**3
+    om = W.omegas(Q, 1 / 0.6)
+    rho, u = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    h_rho = torch.from_numpy(rho).pin_memory()
+    h_u = torch.from_numpy(u).pin_memory()
+    o_rho = torch.empty(shape, dtype=torch.float32).pin_memory()
+    o_u = torch.empty((3,) + shape, dtype=torch.float32).pin_memory()
+    S = lbm.Solver(Q, shape, om)
+    d_rho = torch.empty(shape, dtype=torch.float64, device="cuda")
+    d_u = torch.empty((3,) + shape, dtype=torch.float64, device="cuda")
+    r_out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    u_out = torch.empty((3,) + shape, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def job():
+        d_rho.copy_(h_rho, non_blocking=True)
+        d_u.copy_(h_u, non_blocking=True)
+        lbm.lbm_init_equilibrium(S.ctx, d_rho, d_u)
+        lbm.lbm_step(S.ctx, steps)
+        lbm.lbm_macroscopic(S.ctx, r_out, u_out)
+        o_rho.copy_(r_out, non_blocking=True)
+        o_u.copy_(u_out, non_blocking=True)
+        stream.synchronize()
+
+    job()  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    job()
+    dt = time.perf_counter() - t0
+    h2d = (8 + 24) * N
+    d2h = (4 + 12) * N
+    return {"value": N * steps / dt / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "job": "upload rho,u (FP64, pinned) + init + %d steps + macroscopic + download "
+                   "rho,u (FP32)" % steps}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    barrier = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        barrier = dist.barrier
+
+    from paper_1202_6081_gb300 import build, lbm
+    build()
+    size = args.size
+    S, _, _ = make_solver(lbm, 27, size, "f32", 0.6)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    elapsed = time_steps(torch, S, args.steps, args.warmup, barrier)
+    clocks = sampler.stop() if sampler else None
+    cons = S.conservation()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    cells = size**3
+    value = world * cells * args.steps / elapsed / 1e6
+    peaks, peak_kind = measured_peaks()
+    per_launch = elapsed / args.steps
+    alg_bytes = BYTES_PER_CELL[("q27", "f32")] * cells
+    achieved = alg_bytes / per_launch / 1e9
+    peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_launch * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "D3Q27 Taylor-Green+noise %d^3 periodic, tau=0.6, FP32 storage "
+                               "of f-w" % size,
+                   "cells": cells, "l2": "no flush: inputs larger than L2 (2 x %.1f GB state)"
+                   % (alg_bytes / 2 / 1e9), "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(size),
+                     "peak_source": "%s hbm_gbs (copy), %d B/cell algorithmic" % (
+                         peak_kind, BYTES_PER_CELL[("q27", "f32")])},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "conservation": {"mass": cons[0], "momentum": list(cons[1:])},
+    }
+    del S
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.quick:
+        result["e2e"] = e2e_job(torch, lbm, size, args.steps)
+        torch.cuda.empty_cache()
+        sweep = {}
+        for tau in (0.51, 0.6, 1.0):
+            S, _, _ = make_solver(lbm, 27, size, "f32", tau)
+            t = time_steps(torch, S, 200, 5)
+            sweep["%g" % tau] = cells * 200 / t / 1e6
+            del S
+        result["tau_sweep_mlups"] = sweep
+        torch.cuda.empty_cache()
+        s16 = {}
+        big = 512
+        for st in ("f32", "f16", "bf16"):
+            S, _, _ = make_solver(lbm, 27, big, st, 0.6)
+            t = time_steps(torch, S, 100, 5)
+            mlups = big**3 * 100 / t / 1e6
+            bpc = BYTES_PER_CELL[("q27", st)]
+            s16[st] = {"mlups": mlups, "GB/s": bpc * big**3 * 100 / t / 1e9,
+                       "frac": bpc * big**3 * 100 / t / 1e9 / peak}
+            del S
+            torch.cuda.empty_cache()
+        result["storage_512"] = s16
+        result["cpu_baseline"] = cpu_baseline(size)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) central-moment lattice Boltzmann
+ * library, liblbm.so.
+ *
+ * The method is the three-dimensional central-moment LBM with forcing terms
+ * of Premnath & Banerjee ("On the three-dimensional central moment lattice
+ * Boltzmann method"), on the D3Q27 lattice (Sec. 2-8) and the D3Q15 lattice
+ * (App. G).  One time step is the fused collide-and-stream update
+ *     f~(x, t)          = f(x, t) + K.g(x, t) + S(x, t)   (Eq. cascadedcollision1)
+ *     f(x + e_a, t + 1) = f~_a(x, t)                      (Eq. cascadedstreaming1)
+ * where f is the transformed distribution f-bar = f - S/2 of Sec. 4, g the
+ * cascaded central-moment collision kernel of Sec. 7 and S the
+ * semi-implicit source term of App. E / App. G.
+ *
+ * Conventions shared by every call:
+ *   - Grid: nx * ny * nz cells; cell (x, y, z) has dense index
+ *     c = (z * ny + y) * nx + x.  x is always periodic; y and z are periodic
+ *     or closed by half-way bounce-back walls (Sec. 9), see LBM_WALL_*.
+ *   - Velocity order: the paper's, alpha = 0..Q-1 (Eq. velocityd3qq27 and
+ *     the component lists of Sec. 2 for D3Q27; Eq. velocityd3q15 and the
+ *     matrix of App. G for D3Q15).
+ *   - Dense fields exchanged with the caller are structure-of-arrays:
+ *     distributions [Q][nz][ny][nx], vectors [3][nz][ny][nx], scalars
+ *     [nz][ny][nx].  Every pointer argument named "device" is device memory
+ *     of the GPU that was current at lbm_create; "host" is host memory.
+ *   - Ownership: the caller allocates and frees every device buffer and owns
+ *     every stream.  The library allocates only its context and a small
+ *     reduction scratch, both released by lbm_destroy.
+ *   - Streams: a `void *stream` argument is a cudaStream_t (NULL = the legacy
+ *     default stream).  Every call is asynchronous on that stream except
+ *     lbm_conservation, which synchronises it.
+ *   - Errors: every call returns an lbm_status; nothing throws, aborts or
+ *     prints.  Argument errors are detected before any work is enqueued and
+ *     leave the context unchanged.  A CUDA launch error is reported as
+ *     LBM_ECUDA (the CUDA error string is available from
+ *     lbm_last_cuda_error).
+ *   - Thread safety: one context must not be used from two host threads at
+ *     once; distinct contexts are independent.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { LBM_D3Q15 = 15, LBM_D3Q27 = 27 } lbm_lattice;
+
+/* How the two state buffers hold the distributions.  All arithmetic is FP32
+ * whatever the storage.  LBM_STORE_F32 keeps f - w_a (the deviation from the
+ * lattice weight w_a, the rest state at rho = 1) in FP32; the 16-bit modes
+ * keep (f - w_a) / w_a rounded to nearest-even in FP16 or BF16. */
+typedef enum { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2 } lbm_storage;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,       /* bad argument (null pointer, size, rate, alias) */
+    LBM_ENOMEM = 2,       /* the library's own scratch could not be allocated */
+    LBM_ESTATE = 3,       /* call out of order (e.g. step before bind) */
+    LBM_ECUDA = 4,        /* a CUDA call or kernel launch failed */
+    LBM_ENONFINITE = 5,   /* a conservation sum is NaN or infinite */
+    LBM_EUNSUPPORTED = 6  /* valid request this build does not provide */
+} lbm_status;
+
+/* bc_flags of lbm_create: half-way bounce-back walls on the y faces
+ * (between y = -1 and 0 and between ny - 1 and ny) and/or the z faces. */
+#define LBM_WALL_Y 1u
+#define LBM_WALL_Z 2u
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Create a solver context for one grid.
+ *   lattice  LBM_D3Q27 or LBM_D3Q15.
+ *   nx,ny,nz grid size, each >= 1, ny and nz <= 65535; nx*ny*nz*Q < 2^40.
+ *   omega    host, Q relaxation rates omega_beta of the cascade (Sec. 7);
+ *            entries 0..3 are ignored (collision invariants), the others
+ *            must lie in (0, 2).  omega_4..omega_8 set the shear viscosity
+ *            nu = (1/omega - 1/2)/3 (end of Sec. 7; App. G).
+ *   force    host, 3 values: the uniform body force F (lattice units); used
+ *            when no force field is bound.  NULL means zero.
+ *   bc_flags OR of LBM_WALL_Y / LBM_WALL_Z (0: fully periodic).
+ *   storage  an lbm_storage value.
+ *   out      receives the context (set to NULL on error).
+ * Errors: LBM_EINVAL, LBM_ENOMEM (context allocation), LBM_ECUDA (no usable
+ * device).  The GPU current at this call is the context's device. */
+lbm_status lbm_create(lbm_lattice lattice, int nx, int ny, int nz, const double *omega,
+                      const double *force, unsigned bc_flags, lbm_storage storage,
+                      lbm_ctx **out);
+
+/* Release the context and its reduction scratch (not the caller's buffers).
+ * Safe on NULL.  Work already enqueued must have completed. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Size in bytes of each of the two state buffers the caller must provide:
+ * Q populations of ny * nz rows of a row pitch >= nx elements (a multiple of
+ * 32 elements), in the storage type.  0 for a NULL context. */
+size_t lbm_state_bytes(const lbm_ctx *ctx);
+
+/* Row pitch in elements of the state buffers (see lbm_state_bytes). */
+int lbm_row_pitch(const lbm_ctx *ctx);
+
+/* Attach the caller's two state buffers (device, lbm_state_bytes each,
+ * 256-byte aligned, not overlapping) and an optional per-cell force field
+ * force_field (device, FP32 [3][nz][ny][nx], NULL = the uniform force).
+ * The buffers' contents are undefined until lbm_init_equilibrium or
+ * lbm_set_state.  Rebinding is allowed between steps.
+ * Errors: LBM_EINVAL (null, misaligned or equal buffers). */
+lbm_status lbm_bind(lbm_ctx *ctx, void *f_a, void *f_b, const float *force_field);
+
+/* Replace the uniform body force (host, 3 values; NULL = zero) used by the
+ * following steps when no force field is bound.  Takes effect for work
+ * enqueued after this call (the value is passed by argument to each launch). */
+lbm_status lbm_set_force(lbm_ctx *ctx, const double *force);
+
+/* Replace the relaxation rates (host, Q values, as in lbm_create). */
+lbm_status lbm_set_omega(lbm_ctx *ctx, const double *omega);
+
+/* Set the state to f = f^at(rho, u) - S(F, u)/2 at every cell: f^at is the
+ * attractor state of the collision (the central moments of
+ * Eq. transformedcentralmomentattractors: rho, 0, rho/3, ..., with the
+ * factorised higher orders) and S the source of App. E / App. G, so that
+ * Eqs. densitycalculation and velocitycalculation return rho and u.
+ *   rho device FP64 [nz][ny][nx];  u device FP64 [3][nz][ny][nx].
+ * The paper does not prescribe an initial state; this is the library's
+ * choice.  Errors: LBM_ESTATE (not bound), LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u, void *stream);
+
+/* Load an arbitrary state f (device FP64 [Q][nz][ny][nx], the transformed
+ * distributions f-bar at the current time), converting to the storage type.
+ * Errors: LBM_ESTATE, LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_set_state(lbm_ctx *ctx, const double *f, void *stream);
+
+/* Read the current state back (device FP64 [Q][nz][ny][nx]). */
+lbm_status lbm_get_state(const lbm_ctx *ctx, double *f, void *stream);
+
+/* Advance nsteps >= 0 fused collide-and-stream steps (Eqs. cascadedcollision1
+ * and cascadedstreaming1), one kernel launch per step on `stream`.
+ * Errors: LBM_ESTATE (not bound), LBM_EINVAL (nsteps < 0), LBM_ECUDA. */
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps, void *stream);
+
+/* Density and velocity of the current state, Eqs. densitycalculation and
+ * velocitycalculation (u includes the +F/2 shift):
+ *   rho device FP32 [nz][ny][nx] (may be NULL);  u device FP32 [3][nz][ny][nx]
+ *   (may be NULL). */
+lbm_status lbm_macroscopic(const lbm_ctx *ctx, float *rho, float *u, void *stream);
+
+/* Global mass and momentum of the current state, sum_x rho and
+ * sum_x rho u (with the +F/2 shift), accumulated in FP64 on the GPU
+ * (collision invariants, Sec. 4).  out: host, 4 doubles.  Synchronises
+ * `stream`.  Deterministic (fixed reduction order).
+ * Errors: LBM_ESTATE, LBM_ENOMEM (scratch), LBM_ECUDA, LBM_ENONFINITE (out is
+ * still written). */
+lbm_status lbm_conservation(lbm_ctx *ctx, double out[4], void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *lbm_status_string(lbm_status status);
+
+/* CUDA error string of the context's last LBM_ECUDA (static string; "" if none). */
+const char *lbm_last_cuda_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,303 @@
+// C ABI of liblbm.so (declarations and contracts: include/lbm.h).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/lbm.h"
+#include "kernels.cuh"
+
+namespace lbm {
+LBM_INSTANTIATE(extern, 27)
+LBM_INSTANTIATE(extern, 15)
+}  // namespace lbm
+
+struct lbm_ctx {
+    int Q;
+    lbm_storage storage;
+    lbm::Grid g;
+    float w[27];
+    float F[3];
+    void *buf[2];
+    int cur;  // buffer holding the current state
+    const float *Ffield;
+    bool bound;
+    bool state_set;
+    int device;
+    double *red_scratch;  // partial sums + 4 totals
+    int red_blocks;
+    const char *cuda_error;
+};
+
+namespace {
+
+size_t elem_bytes(lbm_storage st) { return st == LBM_STORE_F32 ? 4 : 2; }
+
+lbm::StepArgs step_args(const lbm_ctx *c) {
+    lbm::StepArgs a;
+    a.g = c->g;
+    for (int b = 0; b < 27; ++b) a.w[b] = c->w[b];
+    for (int i = 0; i < 3; ++i) a.F[i] = c->F[i];
+    a.Ffield = c->Ffield;
+    return a;
+}
+
+bool valid_rates(int Q, const double *omega) {
+    if (!omega) return false;
+    for (int b = 4; b < Q; ++b)
+        if (!(omega[b] > 0.0 && omega[b] < 2.0)) return false;
+    return true;
+}
+
+lbm_status cuda_fail(const lbm_ctx *c, cudaError_t e) {
+    const_cast<lbm_ctx *>(c)->cuda_error = cudaGetErrorString(e);
+    return LBM_ECUDA;
+}
+
+// Dispatch on (Q, storage) to a templated launcher F<Q, T>.
+template <template <int, typename> class Fn, typename... Args>
+cudaError_t dispatch(const lbm_ctx *c, Args &&...args) {
+    switch (c->Q * 4 + int(c->storage)) {
+        case 27 * 4 + LBM_STORE_F32: return Fn<27, float>::run(args...);
+        case 27 * 4 + LBM_STORE_F16: return Fn<27, __half>::run(args...);
+        case 27 * 4 + LBM_STORE_BF16: return Fn<27, __nv_bfloat16>::run(args...);
+        case 15 * 4 + LBM_STORE_F32: return Fn<15, float>::run(args...);
+        case 15 * 4 + LBM_STORE_F16: return Fn<15, __half>::run(args...);
+        case 15 * 4 + LBM_STORE_BF16: return Fn<15, __nv_bfloat16>::run(args...);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int Q, typename T>
+struct StepFn {
+    static cudaError_t run(const void *fin, void *fout, const lbm::StepArgs &a, cudaStream_t s) {
+        return lbm::launch_step<Q, T>(fin, fout, a, s);
+    }
+};
+template <int Q, typename T>
+struct InitFn {
+    static cudaError_t run(void *buf, const lbm::StepArgs &a, const double *rho, const double *u,
+                           cudaStream_t s) {
+        return lbm::launch_init<Q, T>(buf, a, rho, u, s);
+    }
+};
+template <int Q, typename T>
+struct SetFn {
+    static cudaError_t run(void *buf, const lbm::Grid &g, const double *f, cudaStream_t s) {
+        return lbm::launch_set_state<Q, T>(buf, g, f, s);
+    }
+};
+template <int Q, typename T>
+struct GetFn {
+    static cudaError_t run(const void *buf, const lbm::Grid &g, double *f, cudaStream_t s) {
+        return lbm::launch_get_state<Q, T>(buf, g, f, s);
+    }
+};
+template <int Q, typename T>
+struct MacroFn {
+    static cudaError_t run(const void *buf, const lbm::StepArgs &a, float *rho, float *u,
+                           cudaStream_t s) {
+        return lbm::launch_macro<Q, T>(buf, a, rho, u, s);
+    }
+};
+template <int Q, typename T>
+struct ConsFn {
+    static cudaError_t run(const void *buf, const lbm::StepArgs &a, double *part, int blocks,
+                           cudaStream_t s) {
+        return lbm::launch_conservation<Q, T>(buf, a, part, blocks, s);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(lbm_lattice lattice, int nx, int ny, int nz, const double *omega,
+                      const double *force, unsigned bc_flags, lbm_storage storage,
+                      lbm_ctx **out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    const int Q = int(lattice);
+    if (Q != 27 && Q != 15) return LBM_EINVAL;
+    if (nx < 1 || ny < 1 || nz < 1) return LBM_EINVAL;
+    if (ny > 65535 || nz > 65535) return LBM_EINVAL;  // launch grid limits (y, z)
+    if (bc_flags & ~(LBM_WALL_Y | LBM_WALL_Z)) return LBM_EINVAL;
+    if (storage != LBM_STORE_F32 && storage != LBM_STORE_F16 && storage != LBM_STORE_BF16)
+        return LBM_EINVAL;
+    if (!valid_rates(Q, omega)) return LBM_EINVAL;
+    const long long px = ((long long)nx + 31) / 32 * 32;
+    const long long cells = (long long)nx * ny * nz;
+    if (px * ny * nz * Q >= (1LL << 40) || cells >= (1LL << 40)) return LBM_EINVAL;
+    if (force)
+        for (int i = 0; i < 3; ++i)
+            if (!std::isfinite(force[i])) return LBM_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ENOMEM;
+    c->Q = Q;
+    c->storage = storage;
+    c->g.nx = nx;
+    c->g.ny = ny;
+    c->g.nz = nz;
+    c->g.px = int(px);
+    c->g.bc = bc_flags;
+    c->g.plane = px * ny;
+    c->g.pop = px * ny * nz;
+    for (int b = 0; b < 27; ++b) c->w[b] = (b >= 4 && b < Q) ? float(omega[b]) : 0.0f;
+    for (int i = 0; i < 3; ++i) c->F[i] = force ? float(force[i]) : 0.0f;
+    c->cur = 0;
+    c->device = dev;
+    c->cuda_error = "";
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c) {
+    if (!c) return;
+    if (c->red_scratch) cudaFree(c->red_scratch);
+    delete c;
+}
+
+size_t lbm_state_bytes(const lbm_ctx *c) {
+    if (!c) return 0;
+    return size_t(c->Q) * size_t(c->g.pop) * elem_bytes(c->storage);
+}
+
+int lbm_row_pitch(const lbm_ctx *c) { return c ? c->g.px : 0; }
+
+lbm_status lbm_bind(lbm_ctx *c, void *f_a, void *f_b, const float *force_field) {
+    if (!c || !f_a || !f_b || f_a == f_b) return LBM_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(f_a) | reinterpret_cast<uintptr_t>(f_b)) & 255u)
+        return LBM_EINVAL;
+    const size_t bytes = lbm_state_bytes(c);
+    const char *a = static_cast<const char *>(f_a), *b = static_cast<const char *>(f_b);
+    if (a < b + bytes && b < a + bytes) return LBM_EINVAL;  // overlap
+    if (force_field && (reinterpret_cast<uintptr_t>(force_field) & 3u)) return LBM_EINVAL;
+    c->buf[0] = f_a;
+    c->buf[1] = f_b;
+    c->cur = 0;
+    c->Ffield = force_field;
+    c->bound = true;
+    c->state_set = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_force(lbm_ctx *c, const double *force) {
+    if (!c) return LBM_EINVAL;
+    if (force)
+        for (int i = 0; i < 3; ++i)
+            if (!std::isfinite(force[i])) return LBM_EINVAL;
+    for (int i = 0; i < 3; ++i) c->F[i] = force ? float(force[i]) : 0.0f;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_omega(lbm_ctx *c, const double *omega) {
+    if (!c || !valid_rates(c->Q, omega)) return LBM_EINVAL;
+    for (int b = 4; b < c->Q; ++b) c->w[b] = float(omega[b]);
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx *c, const double *rho, const double *u, void *stream) {
+    if (!c || !rho || !u) return LBM_EINVAL;
+    if (!c->bound) return LBM_ESTATE;
+    const lbm::StepArgs a = step_args(c);
+    cudaError_t e = dispatch<InitFn>(c, c->buf[c->cur], a, rho, u, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->state_set = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx *c, const double *f, void *stream) {
+    if (!c || !f) return LBM_EINVAL;
+    if (!c->bound) return LBM_ESTATE;
+    cudaError_t e = dispatch<SetFn>(c, c->buf[c->cur], c->g, f, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->state_set = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_state(const lbm_ctx *c, double *f, void *stream) {
+    if (!c || !f) return LBM_EINVAL;
+    if (!c->bound || !c->state_set) return LBM_ESTATE;
+    cudaError_t e = dispatch<GetFn>(c, (const void *)c->buf[c->cur], c->g, f,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *c, int nsteps, void *stream) {
+    if (!c || nsteps < 0) return LBM_EINVAL;
+    if (!c->bound || !c->state_set) return LBM_ESTATE;
+    const lbm::StepArgs a = step_args(c);
+    for (int s = 0; s < nsteps; ++s) {
+        cudaError_t e = dispatch<StepFn>(c, (const void *)c->buf[c->cur], c->buf[1 - c->cur], a,
+                                         (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        c->cur = 1 - c->cur;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_macroscopic(const lbm_ctx *c, float *rho, float *u, void *stream) {
+    if (!c) return LBM_EINVAL;
+    if (!c->bound || !c->state_set) return LBM_ESTATE;
+    if (!rho && !u) return LBM_OK;
+    const lbm::StepArgs a = step_args(c);
+    cudaError_t e =
+        dispatch<MacroFn>(c, (const void *)c->buf[c->cur], a, rho, u, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return LBM_OK;
+}
+
+lbm_status lbm_conservation(lbm_ctx *c, double out[4], void *stream) {
+    if (!c || !out) return LBM_EINVAL;
+    if (!c->bound || !c->state_set) return LBM_ESTATE;
+    const long long N = (long long)c->g.nx * c->g.ny * c->g.nz;
+    const int blocks = lbm::conservation_blocks(N);
+    if (!c->red_scratch || c->red_blocks < blocks) {
+        if (c->red_scratch) cudaFree(c->red_scratch);
+        c->red_scratch = nullptr;
+        if (cudaMalloc(&c->red_scratch, sizeof(double) * (4 * size_t(blocks) + 4)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return LBM_ENOMEM;
+        }
+        c->red_blocks = blocks;
+    }
+    const lbm::StepArgs a = step_args(c);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = dispatch<ConsFn>(c, (const void *)c->buf[c->cur], a, c->red_scratch, blocks, s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    double *tot = c->red_scratch + 4 * size_t(c->red_blocks);
+    e = lbm::launch_reduce_final(c->red_scratch, blocks, tot, s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    double h[4];
+    e = cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    out[0] = double(N) + h[0];  // the rest state carries mass 1 per cell
+    out[1] = h[1];
+    out[2] = h[2];
+    out[3] = h[3];
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(out[k])) return LBM_ENONFINITE;
+    return LBM_OK;
+}
+
+const char *lbm_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "LBM_OK";
+        case LBM_EINVAL: return "LBM_EINVAL: invalid argument";
+        case LBM_ENOMEM: return "LBM_ENOMEM: allocation failed";
+        case LBM_ESTATE: return "LBM_ESTATE: call out of order";
+        case LBM_ECUDA: return "LBM_ECUDA: CUDA error";
+        case LBM_ENONFINITE: return "LBM_ENONFINITE: non-finite conservation sum";
+        case LBM_EUNSUPPORTED: return "LBM_EUNSUPPORTED: not provided by this build";
+        default: return "unknown lbm_status";
+    }
+}
+
+const char *lbm_last_cuda_error(const lbm_ctx *c) { return c ? c->cuda_error : ""; }
+
+}  // extern "C"

@@ -1,0 +1,233 @@
+// Lattice constants, state storage and the pull-streaming gather shared by
+// the kernels of liblbm.so.
+//
+// State layout in HBM: structure of arrays, population-major,
+//   buf[alpha][z][y][x_pitched],  alpha in the paper's velocity order,
+// x fastest with a row pitch `px` (multiple of 32 elements) so that every
+// row starts on a 128-byte boundary.  Each population plane is therefore a
+// contiguous stream, and a warp of 32 consecutive x reads 128 bytes (FP32)
+// or 64 bytes (16-bit) per population.
+//
+// The buffer holds the post-collision values of the previous step
+// (f~ of Eq. cascadedcollision1).  A step pulls: the pre-collision value of
+// population alpha at cell x is f~_alpha(x - e_alpha) (Eq. cascadedstreaming1
+// read backwards), or, when x - e_alpha lies beyond a half-way bounce-back
+// wall, the reversed population of the same cell, f~_opp(alpha)(x).
+//
+// Stored values are deviations from the lattice weights, f - w_alpha (FP32),
+// or (f - w_alpha) / w_alpha (FP16/BF16).  Arithmetic on deviations keeps the
+// O(1) rest state out of every rounding.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr unsigned kWallY = 1u;
+constexpr unsigned kWallZ = 2u;
+
+// ---------------------------------------------------------------- velocities
+// D3Q27 in the paper's order (Sec. 2): rest, the 6 axis vectors, the 12
+// edge vectors (xy, xz, yz planes), the 8 corners.
+__host__ __device__ constexpr int q27_e(int a, int c) {
+    const signed char t[27][3] = {
+        {0, 0, 0},  {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},   {0, 0, -1},
+        {1, 1, 0},  {-1, 1, 0},  {1, -1, 0},  {-1, -1, 0}, {1, 0, 1},   {-1, 0, 1},  {1, 0, -1},
+        {-1, 0, -1}, {0, 1, 1},  {0, -1, 1},  {0, 1, -1},  {0, -1, -1}, {1, 1, 1},   {-1, 1, 1},
+        {1, -1, 1}, {-1, -1, 1}, {1, 1, -1},  {-1, 1, -1}, {1, -1, -1}, {-1, -1, -1}};
+    return t[a][c];
+}
+
+// D3Q15 in the paper's order (App. G): rest, 6 axis vectors, 8 corners.
+__host__ __device__ constexpr int q15_e(int a, int c) {
+    const signed char t[15][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                  {0, 0, 1},   {0, 0, -1},  {1, 1, 1},  {-1, 1, 1}, {1, -1, 1},
+                                  {-1, -1, 1}, {1, 1, -1},  {-1, 1, -1}, {1, -1, -1},
+                                  {-1, -1, -1}};
+    return t[a][c];
+}
+
+template <int Q>
+__host__ __device__ constexpr int ex(int a) { return Q == 27 ? q27_e(a, 0) : q15_e(a, 0); }
+template <int Q>
+__host__ __device__ constexpr int ey(int a) { return Q == 27 ? q27_e(a, 1) : q15_e(a, 1); }
+template <int Q>
+__host__ __device__ constexpr int ez(int a) { return Q == 27 ? q27_e(a, 2) : q15_e(a, 2); }
+
+// slot of the velocity (cx, cy, cz), -1 if it is not in the set
+template <int Q>
+__host__ __device__ constexpr int slot_of(int cx, int cy, int cz) {
+    for (int a = 0; a < Q; ++a)
+        if (ex<Q>(a) == cx && ey<Q>(a) == cy && ez<Q>(a) == cz) return a;
+    return -1;
+}
+
+template <int Q>
+__host__ __device__ constexpr int opposite(int a) { return slot_of<Q>(-ex<Q>(a), -ey<Q>(a), -ez<Q>(a)); }
+
+// Lattice weights: the rest state (rho = 1, u = 0) of each lattice.
+// D3Q27 factorises per axis into (1/6, 2/3, 1/6); D3Q15: 2/9, 1/9, 1/72.
+template <int Q>
+__host__ __device__ constexpr double weight(int a) {
+    if (Q == 27) {
+        const int n = ex<27>(a) * ex<27>(a) + ey<27>(a) * ey<27>(a) + ez<27>(a) * ez<27>(a);
+        return n == 0 ? 8.0 / 27.0 : n == 1 ? 2.0 / 27.0 : n == 2 ? 1.0 / 54.0 : 1.0 / 216.0;
+    } else {
+        const int n = ex<15>(a) * ex<15>(a) + ey<15>(a) * ey<15>(a) + ez<15>(a) * ez<15>(a);
+        return n == 0 ? 2.0 / 9.0 : n == 1 ? 1.0 / 9.0 : 1.0 / 72.0;
+    }
+}
+
+// ------------------------------------------------------------------- storage
+template <typename T>
+struct Storage;
+
+template <>
+struct Storage<float> {
+    static constexpr bool kScaled = false;
+    __device__ __forceinline__ static float load(const float *p) { return __ldg(p); }
+    __device__ __forceinline__ static void store(float *p, float v) { __stcs(p, v); }
+    __device__ __forceinline__ static float from_f(float v) { return v; }
+};
+
+template <>
+struct Storage<__half> {
+    static constexpr bool kScaled = true;
+    __device__ __forceinline__ static float load(const __half *p) {
+        return __half2float(__ldg(p));
+    }
+    __device__ __forceinline__ static void store(__half *p, float v) {
+        __stcs(reinterpret_cast<unsigned short *>(p), __half_as_ushort(__float2half_rn(v)));
+    }
+};
+
+template <>
+struct Storage<__nv_bfloat16> {
+    static constexpr bool kScaled = true;
+    __device__ __forceinline__ static float load(const __nv_bfloat16 *p) {
+        return __bfloat162float(__ldg(p));
+    }
+    __device__ __forceinline__ static void store(__nv_bfloat16 *p, float v) {
+        __stcs(reinterpret_cast<unsigned short *>(p),
+               __bfloat16_as_ushort(__float2bfloat16_rn(v)));
+    }
+};
+
+// Stored value -> deviation f - w (FP32), and back.
+template <int Q, typename T>
+__device__ __forceinline__ float load_dev(const T *p, int a) {
+    const float v = Storage<T>::load(p);
+    if (Storage<T>::kScaled) return v * float(weight<Q>(a));
+    return v;
+}
+
+template <int Q, typename T>
+__device__ __forceinline__ void store_dev(T *p, int a, float dev) {
+    if (Storage<T>::kScaled)
+        Storage<T>::store(p, dev * float(1.0 / weight<Q>(a)));
+    else
+        Storage<T>::store(p, dev);
+}
+
+// ---------------------------------------------------------------------- grid
+struct Grid {
+    int nx, ny, nz;   // cells
+    int px;           // row pitch in elements
+    unsigned bc;      // kWallY | kWallZ
+    long long plane;  // px * ny
+    long long pop;    // px * ny * nz: distance between populations
+};
+
+// Source coordinates of the pull for one cell.  Index 0, 1, 2 of each array
+// is the velocity component -1, 0, +1; the source along an axis is the cell
+// coordinate minus the component.  wall[...] is set where that source lies
+// beyond a bounce-back wall.
+struct PullSources {
+    int xs[3];
+    long long row[3][3];  // (zs * ny + ys) * px for (cy, cz)
+    bool wall[3][3];      // bounce back for (cy, cz)
+    long long own;        // (z * ny + y) * px + x
+};
+
+__device__ __forceinline__ PullSources pull_sources(const Grid &g, int x, int y, int z) {
+    PullSources s;
+    s.xs[0] = (x + 1 == g.nx) ? 0 : x + 1;
+    s.xs[1] = x;
+    s.xs[2] = (x == 0) ? g.nx - 1 : x - 1;
+    int ys[3], zs[3];
+    bool wy[3], wz[3];
+    ys[1] = y;
+    wy[1] = false;
+    ys[0] = (y + 1 == g.ny) ? 0 : y + 1;
+    wy[0] = (y + 1 == g.ny) && (g.bc & kWallY);
+    ys[2] = (y == 0) ? g.ny - 1 : y - 1;
+    wy[2] = (y == 0) && (g.bc & kWallY);
+    zs[1] = z;
+    wz[1] = false;
+    zs[0] = (z + 1 == g.nz) ? 0 : z + 1;
+    wz[0] = (z + 1 == g.nz) && (g.bc & kWallZ);
+    zs[2] = (z == 0) ? g.nz - 1 : z - 1;
+    wz[2] = (z == 0) && (g.bc & kWallZ);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            s.row[j][k] = ((long long)zs[k] * g.ny + ys[j]) * g.px;
+            s.wall[j][k] = wy[j] || wz[k];
+        }
+    s.own = ((long long)z * g.ny + y) * g.px + x;
+    return s;
+}
+
+// Pre-collision deviations f_alpha(x) - w_alpha of one cell (slot order).
+template <int Q, typename T>
+__device__ __forceinline__ void gather(const T *__restrict__ fin, const Grid &g,
+                                       const PullSources &s, float (&f)[Q]) {
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int j = ey<Q>(a) + 1, k = ez<Q>(a) + 1, i = ex<Q>(a) + 1;
+        long long idx;
+        int slot;
+        if (s.wall[j][k]) {
+            slot = opposite<Q>(a);
+            idx = (long long)slot * g.pop + s.own;
+        } else {
+            slot = a;
+            idx = (long long)a * g.pop + s.row[j][k] + s.xs[i];
+        }
+        const float v = Storage<T>::load(fin + idx);
+        // the weight of a slot and of its opposite are equal
+        f[a] = Storage<T>::kScaled ? v * float(weight<Q>(a)) : v;
+        (void)slot;
+    }
+}
+
+// Store post-collision deviations of one cell at its own position.
+template <int Q, typename T>
+__device__ __forceinline__ void store_own(T *__restrict__ fout, const Grid &g, long long own,
+                                          const float (&f)[Q]) {
+#pragma unroll
+    for (int a = 0; a < Q; ++a) store_dev<Q, T>(fout + (long long)a * g.pop + own, a, f[a]);
+}
+
+// Inverse of the pull: place the pre-collision values f_alpha(x) of one cell
+// where the next pull will read them (used to load a state).
+template <int Q, typename T>
+__device__ __forceinline__ void scatter_state(T *__restrict__ buf, const Grid &g,
+                                              const PullSources &s, const float (&f)[Q]) {
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int j = ey<Q>(a) + 1, k = ez<Q>(a) + 1, i = ex<Q>(a) + 1;
+        if (s.wall[j][k]) {
+            const int o = opposite<Q>(a);
+            store_dev<Q, T>(buf + (long long)o * g.pop + s.own, o, f[a]);
+        } else {
+            store_dev<Q, T>(buf + (long long)a * g.pop + s.row[j][k] + s.xs[i], a, f[a]);
+        }
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,254 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 arithmetic and storage of f - w):
+  * one step from an arbitrary state: |f_gpu - f_oracle| <= 2e-6 per
+    population (values up to ~0.1, deviations up to ~0.3; FP32 rounding of
+    ~20 dependent operations with rates up to 1.9);
+  * after many steps: relative L2 of density and velocity <= 1e-5 (the bar
+    stated for FP32 storage);
+  * 16-bit storage: relative L2 of velocity vs the oracle <= 1e-3 (FP16) and
+    a looser bound for BF16, whose 8-bit significand cannot meet 1e-3.
+"""
+import numpy as np
+import pytest
+
+import analytic
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1202_6081_gb300 import build
+    from paper_1202_6081_gb300 import lbm as mod
+    build()
+    mod.load()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def gpu_state(S):
+    torch.cuda.synchronize()
+    return S.get_state().cpu().numpy()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+GRIDS = [(7, 3, 5), (9, 10, 37), (2, 33, 64)]  # (nz, ny, nx): ragged rows, several warps
+
+
+@pytest.mark.parametrize("Q", [27, 15])
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", GRIDS)
+def test_one_step_from_random_state(lbm, orc, Q, bc, shape):
+    f0 = W.random_field_state(shape, Q, seed=100 + bc, spread=0.5)
+    om = W.random_omegas(Q, seed=5)
+    F = np.array([3e-3, -2e-3, 1e-3])
+    S = lbm.Solver(Q, shape, om, force=F, walls=bc)
+    S.set_state(f0)
+    S.step(1)
+    got = gpu_state(S)
+    want = orc.run(Q, shape, f0, F, om, 1, bc=bc)
+    assert np.abs(got - want).max() <= 2e-6
+
+
+@pytest.mark.parametrize("Q", [27, 15])
+def test_one_step_with_force_field(lbm, orc, Q):
+    shape = (6, 11, 35)
+    f0 = W.random_field_state(shape, Q, seed=7, spread=0.3)
+    om = W.random_omegas(Q, seed=8)
+    F = W.rng(9).uniform(-5e-3, 5e-3, (3,) + shape)
+    S = lbm.Solver(Q, shape, om, force=F, walls=3)
+    S.set_state(f0)
+    S.step(1)
+    want = orc.run(Q, shape, f0, F.astype(np.float32).astype(np.float64), om, 1, bc=3)
+    assert np.abs(gpu_state(S) - want).max() <= 2e-6
+
+
+@pytest.mark.parametrize("Q", [27, 15])
+def test_set_get_roundtrip_fp32(lbm, orc, Q):
+    shape = (4, 5, 33)
+    f0 = W.random_field_state(shape, Q, seed=11)
+    e, _, _, _ = orc.lattice(Q)
+    S = lbm.Solver(Q, shape, W.omegas(Q, 1.2), walls=3)
+    S.set_state(f0)
+    got = gpu_state(S)
+    w = orc.equilibrium(Q, np.ones((1, 1, 1)), np.zeros((3, 1, 1, 1)), np.zeros(3))[:, 0, 0, 0]
+    want = (f0 - w[:, None, None, None]).astype(np.float32).astype(np.float64) + \
+        w[:, None, None, None]
+    np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("Q", [27, 15])
+def test_init_equilibrium_matches_oracle(lbm, orc, Q):
+    shape = (5, 9, 34)
+    r = W.rng(12)
+    rho = r.uniform(0.95, 1.05, shape)
+    u = r.uniform(-0.05, 0.05, (3,) + shape)
+    F = r.uniform(-1e-3, 1e-3, (3,) + shape)
+    S = lbm.Solver(Q, shape, W.omegas(Q, 1.3), force=F, walls=1)
+    S.init_equilibrium(rho, u)
+    want = orc.equilibrium(Q, rho, u, F.astype(np.float32).astype(np.float64))
+    assert np.abs(gpu_state(S) - want).max() <= 2e-7
+
+
+@pytest.mark.parametrize("Q", [27, 15])
+def test_macroscopic_and_conservation_match_oracle(lbm, orc, Q):
+    shape = (6, 7, 40)
+    f0 = W.random_field_state(shape, Q, seed=13, spread=0.2)
+    F = np.array([1e-3, 2e-3, -1e-3])
+    S = lbm.Solver(Q, shape, W.omegas(Q, 1.1), force=F)
+    S.set_state(f0)
+    rho, u = S.macroscopic()
+    rho_o, u_o = orc.macroscopic(Q, f0, F)
+    assert np.abs(rho.cpu().numpy() - rho_o).max() <= 2e-7
+    assert np.abs(u.cpu().numpy() - u_o).max() <= 2e-7
+    cons = S.conservation()
+    want = np.array([rho_o.sum(), *(rho_o * u_o).reshape(3, -1).sum(1)])
+    np.testing.assert_allclose(cons, want, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("Q", [27, 15])
+def test_conservation_over_steps(lbm, Q):
+    """Periodic, uniform force: mass constant, momentum grows by N F per step."""
+    shape = (16, 16, 32)
+    N = 16 * 16 * 32
+    F = np.array([1e-5, -2e-5, 5e-6])
+    rho, u = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    S = lbm.Solver(Q, shape, W.omegas(Q, 1 / 0.6), force=F)
+    S.init_equilibrium(rho, u)
+    c0 = S.conservation()
+    S.step(50)
+    c1 = S.conservation()
+    assert abs(c1[0] - c0[0]) <= 1e-9 * N
+    np.testing.assert_allclose(c1[1:] - c0[1:], 50 * N * F, rtol=1e-4, atol=1e-8)
+
+
+@pytest.mark.parametrize("Q", [27, 15])
+def test_taylor_green_32cubed_100_steps(lbm, orc, Q):
+    """The 32^3 periodic Taylor-Green workload (u0 = 0.02, rho = 1, tau = 0.6,
+    other rates 1, no force, 100 steps): density and velocity within 1e-5
+    relative L2 of the FP64 oracle."""
+    shape = (32, 32, 32)
+    om = W.omegas(Q, 1 / 0.6)
+    rho0, u0 = W.taylor_green(shape, u0=0.02)
+    S = lbm.Solver(Q, shape, om)
+    S.init_equilibrium(rho0, u0)
+    S.step(100)
+    f_gpu = gpu_state(S)
+    f_or = orc.run(Q, shape, orc.equilibrium(Q, rho0, u0, np.zeros(3)), np.zeros(3), om, 100)
+    r_g, u_g = orc.macroscopic(Q, f_gpu, np.zeros(3))
+    r_o, u_o = orc.macroscopic(Q, f_or, np.zeros(3))
+    assert rel_l2(r_g, r_o) <= 1e-5
+    assert rel_l2(u_g, u_o) <= 1e-5
+    # the density fluctuation itself (rho - 1 ~ 1e-4) stays within 1e-3
+    assert rel_l2(r_g - 1, r_o - 1) <= 1e-3
+
+
+@pytest.mark.parametrize("Q", [27, 15])
+def test_walled_channel_with_force_field_matches_oracle(lbm, orc, Q):
+    shape = (9, 10, 13)
+    om = W.omegas(Q, 1.25)
+    F = W.rng(14).uniform(-1e-4, 1e-4, (3,) + shape) + np.array([1e-4, 0, 0])[:, None, None,
+                                                                              None]
+    F32 = F.astype(np.float32).astype(np.float64)
+    rho0, u0 = W.taylor_green(shape, u0=0.01, noise=1e-3)
+    S = lbm.Solver(Q, shape, om, force=F, walls=3)
+    S.init_equilibrium(rho0, u0)
+    S.step(60)
+    f_or = orc.run(Q, shape, orc.equilibrium(Q, rho0, u0, F32), F32, om, 60, bc=3)
+    f_gpu = gpu_state(S)
+    w = orc.equilibrium(Q, np.ones((1, 1, 1)), np.zeros((3, 1, 1, 1)), np.zeros(3))
+    assert rel_l2(f_gpu - w, f_or - w) <= 1e-5
+    r_g, u_g = orc.macroscopic(Q, f_gpu, F32)
+    r_o, u_o = orc.macroscopic(Q, f_or, F32)
+    assert rel_l2(u_g, u_o) <= 1e-5
+
+
+@pytest.mark.parametrize("Q", [15, 27])
+def test_square_channel_steady_state_vs_series(lbm, Q):
+    """16 x 64 x 64 body-force channel (x periodic, half-way bounce-back walls
+    on y and z), F_x = 1e-6, tau = 0.8, 20000 steps: the x-averaged u_x(y, z)
+    matches the square-duct series (Eq. ductFourier, a = 32) to 1e-2."""
+    shape = (64, 64, 16)
+    om = W.omegas(Q, 1 / 0.8)
+    F = np.array([1e-6, 0.0, 0.0])
+    S = lbm.Solver(Q, shape, om, force=F, walls=3)
+    S.init_equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    S.step(20000)
+    _, u = S.macroscopic()
+    ux = u[0].double().mean(dim=2).cpu().numpy()  # [z, y]
+    c = np.arange(64) + 0.5 - 32
+    Z, Y = np.meshgrid(c, c, indexing="ij")
+    ua = analytic.duct_profile(Y, Z, 32.0, 1e-6, analytic.viscosity(1 / 0.8))
+    assert rel_l2(ux, ua) <= 1e-2
+
+
+@pytest.mark.parametrize("storage,bound", [("f16", 1e-3), ("bf16", 2e-2)])
+def test_16bit_storage_taylor_green(lbm, orc, storage, bound):
+    """D3Q27 Taylor-Green + noise, 32^3, 100 steps, 16-bit storage of
+    (f - w)/w with FP32 arithmetic: velocity within the stated bound of the
+    FP64 oracle (FP16 meets 1e-3; BF16 is reported, not held to it)."""
+    Q = 27
+    shape = (32, 32, 32)
+    om = W.omegas(Q, 1 / 0.6)
+    rho0, u0 = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    S = lbm.Solver(Q, shape, om, storage=storage)
+    S.init_equilibrium(rho0, u0)
+    S.step(100)
+    f_gpu = gpu_state(S)
+    f_or = orc.run(Q, shape, orc.equilibrium(Q, rho0, u0, np.zeros(3)), np.zeros(3), om, 100)
+    _, u_g = orc.macroscopic(Q, f_gpu, np.zeros(3))
+    r_o, u_o = orc.macroscopic(Q, f_or, np.zeros(3))
+    err = rel_l2(u_g, u_o)
+    print("16-bit %s: rel L2 u = %.3e" % (storage, err))
+    assert err <= bound
+
+
+def test_full_size_sampled_step_256(lbm, orc):
+    """The 256^3 Taylor-Green + noise workload in the bench's launch
+    configuration: after 5 GPU steps, one more GPU step is checked on 16
+    sampled cells against the oracle's collision of the 27 upstream cells,
+    and mass and momentum are conserved."""
+    Q = 27
+    shape = (256, 256, 256)
+    om = W.omegas(Q, 1 / 0.6)
+    rho0, u0 = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    S = lbm.Solver(Q, shape, om)
+    S.init_equilibrium(rho0, u0)
+    c0 = S.conservation()
+    S.step(5)
+    cells = W.sample_cells(shape, 16)
+    e, _, _, _ = orc.lattice(Q)
+    nz, ny, nx = shape
+    zz, yy, xx = np.unravel_index(cells, shape)
+    # upstream cells x - e_alpha of each sample
+    up = np.stack([np.ravel_multi_index(((zz - e[a, 2]) % nz, (yy - e[a, 1]) % ny,
+                                         (xx - e[a, 0]) % nx), shape) for a in range(Q)], 1)
+    f5 = S.get_state().reshape(Q, -1)
+    idx = torch.as_tensor(up.ravel(), device=f5.device)
+    before = f5[:, idx].T.cpu().numpy()  # [16*Q, Q]
+    del f5
+    S.step(1)
+    f6 = S.get_state().reshape(Q, -1)[:, torch.as_tensor(cells, device="cuda")].cpu().numpy()
+    post, _, _ = orc.collide(Q, before, np.zeros((before.shape[0], 3)), om)
+    post = post.reshape(16, Q, Q)
+    want = np.stack([post[:, a, a] for a in range(Q)])  # population a from upstream a
+    assert np.abs(f6 - want).max() <= 2e-6
+    c1 = S.conservation()
+    N = 256**3
+    assert abs(c1[0] - c0[0]) <= 1e-8 * N
+    np.testing.assert_allclose(c1[1:], c0[1:], atol=1e-6 * N * 1e-3)
