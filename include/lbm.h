@@ -73,7 +73,9 @@ typedef struct lbm_ctx lbm_ctx;
 
 /* Create a solver context for one grid.
  *   lattice  LBM_D3Q27 or LBM_D3Q15.
- *   nx,ny,nz grid size, each >= 1, ny and nz <= 65535; nx*ny*nz*Q < 2^40.
+ *   nx,ny,nz grid size, each >= 1, ny and nz <= 65535, and
+ *            nx*ny*nz < 2^31 (one population plane is addressed with 32-bit
+ *            offsets; 1024^3 fits).
  *   omega    host, Q relaxation rates omega_beta of the cascade (Sec. 7);
  *            entries 0..3 are ignored (collision invariants), the others
  *            must lie in (0, 2).  omega_4..omega_8 set the shear viscosity
@@ -147,8 +149,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps, void *stream);
 lbm_status lbm_macroscopic(const lbm_ctx *ctx, float *rho, float *u, void *stream);
 
 /* Global mass and momentum of the current state, sum_x rho and
- * sum_x rho u (with the +F/2 shift), accumulated in FP64 on the GPU
- * (collision invariants, Sec. 4).  out: host, 4 doubles.  Synchronises
+ * sum_x rho u (with the +F/2 shift): per-cell moments in FP32, sums across
+ * cells in FP64 on the GPU (collision invariants, Sec. 4).  out: host, 4 doubles.  Synchronises
  * `stream`.  Deterministic (fixed reduction order).
  * Errors: LBM_ESTATE, LBM_ENOMEM (scratch), LBM_ECUDA, LBM_ENONFINITE (out is
  * still written). */

@@ -127,7 +127,8 @@ lbm_status lbm_create(lbm_lattice lattice, int nx, int ny, int nz, const double 
     if (!valid_rates(Q, omega)) return LBM_EINVAL;
     const long long px = ((long long)nx + 31) / 32 * 32;
     const long long cells = (long long)nx * ny * nz;
-    if (px * ny * nz * Q >= (1LL << 40) || cells >= (1LL << 40)) return LBM_EINVAL;
+    // population planes are addressed with 32-bit element offsets
+    if (px * ny * nz >= (1LL << 31) || cells >= (1LL << 31)) return LBM_EINVAL;
     if (force)
         for (int i = 0; i < 3; ++i)
             if (!std::isfinite(force[i])) return LBM_EINVAL;
@@ -254,7 +255,7 @@ lbm_status lbm_conservation(lbm_ctx *c, double out[4], void *stream) {
     if (!c || !out) return LBM_EINVAL;
     if (!c->bound || !c->state_set) return LBM_ESTATE;
     const long long N = (long long)c->g.nx * c->g.ny * c->g.nz;
-    const int blocks = lbm::conservation_blocks(N);
+    const int blocks = lbm::conservation_blocks(c->g);
     if (!c->red_scratch || c->red_blocks < blocks) {
         if (c->red_scratch) cudaFree(c->red_scratch);
         c->red_scratch = nullptr;

@@ -30,194 +30,212 @@
 #pragma once
 
 #include "lattice.cuh"
+#include "vec2.cuh"
 
 namespace lbm {
 
 // slot (paper order) of the D3Q27 velocity with components (i-1, j-1, k-1)
 __host__ __device__ constexpr int s27(int i, int j, int k) { return slot_of<27>(i - 1, j - 1, k - 1); }
 
-struct RelaxRates27 {
-    float w[27];  // omega_beta; 0..3 unused
+// Relaxation rates as the collision consumes them: omega, -omega and
+// 1 - omega per beta (0..3 unused), in the value type V (float, or f2 with
+// both lanes equal).
+template <typename V>
+struct Rates27 {
+    V w[27];
+    V nw[27];
+    V omw[27];
 };
 
-// 1-D shift of the triple (f(-1), f(0), f(+1)) to central moments about u.
-// In: raw sums already formed (s0 = a + b + c, s1 = c - a, s2 = a + c).
-__device__ __forceinline__ void central_from_sums(float u, float &m0, float &m1, float &m2) {
-    // m0 = s0; m1 = s1 - u s0; m2 = s2 - 2 u s1 + u^2 s0 = s2 - u (s1 + m1)
-    const float k1 = fmaf(-u, m0, m1);
-    const float k2 = fmaf(-u, m1 + k1, m2);
+// 1-D shift of raw sums (m0, m1, m2) = (sum f, sum e f, sum e^2 f) of a line
+// to central moments about u:  k1 = m1 - u m0,  k2 = m2 - 2 u m1 + u^2 m0.
+// nu = -u.
+template <typename V>
+__device__ __forceinline__ void central_from_sums(V nu, V &m0, V &m1, V &m2) {
+    const V k1 = vfma(nu, m0, m1);
+    const V k2 = vfma(nu, m1 + k1, m2);
     m1 = k1;
     m2 = k2;
 }
 
-__device__ __forceinline__ void sums(float a, float b, float c, float &s0, float &s1, float &s2) {
-    const float ac = a + c;
+// raw sums of the line (a, b, c) = (f(-1), f(0), f(+1))
+template <typename V>
+__device__ __forceinline__ void sums(V a, V b, V c, V &s0, V &s1, V &s2) {
+    const V ac = a + c;
     s0 = ac + b;
     s1 = c - a;
     s2 = ac;
 }
 
 // Inverse: central moments (k0, k1, k2) about u -> (f(-1), f(0), f(+1)).
-__device__ __forceinline__ void dist_from_central(float u, float k0, float k1, float k2, float &a,
-                                                  float &b, float &c) {
-    const float m1 = fmaf(u, k0, k1);      // raw first moment
-    const float m2 = fmaf(u, k1 + m1, k2); // raw second moment
+template <typename V>
+__device__ __forceinline__ void dist_from_central(V u, V k0, V k1, V k2, V &a, V &b, V &c) {
+    const V half = splat<V>(0.5f);
+    const V m1 = vfma(u, k0, k1);      // raw first moment
+    const V m2 = vfma(u, k1 + m1, k2); // raw second moment
     b = k0 - m2;
-    c = 0.5f * (m2 + m1);
-    a = 0.5f * (m2 - m1);
+    c = half * (m2 + m1);
+    a = half * (m2 - m1);
 }
 
 // Relax the deviation central moments D[m][n][p] (= kappa - kappa^w,
 // source included) in place.  drho = rho - 1.
-__device__ __forceinline__ void relax27(float (&D)[3][3][3], float ux, float uy, float uz,
-                                        float drho, const RelaxRates27 &r) {
-    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-    const float third = 1.0f / 3.0f;
-    const float Kwx = third + ux2, Kwy = third + uy2, Kwz = third + uz2;
+template <typename V>
+__device__ __forceinline__ void relax27(V (&D)[3][3][3], V ux, V uy, V uz, V drho,
+                                        const Rates27<V> &r) {
+    const V third = splat<V>(1.0f / 3.0f), sixth = splat<V>(1.0f / 6.0f);
+    const V half = splat<V>(0.5f), two = splat<V>(2.0f);
+    const V ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const V Kwx = third + ux2, Kwy = third + uy2, Kwz = third + uz2;
 
     // order 2, off-diagonal: attractor 0, kappa^w = u_i u_j
-    D[1][1][0] = fmaf(1.0f - r.w[4], D[1][1][0], -r.w[4] * ux * uy);
-    D[1][0][1] = fmaf(1.0f - r.w[5], D[1][0][1], -r.w[5] * ux * uz);
-    D[0][1][1] = fmaf(1.0f - r.w[6], D[0][1][1], -r.w[6] * uy * uz);
+    D[1][1][0] = vfma(r.omw[4], D[1][1][0], r.nw[4] * (ux * uy));
+    D[1][0][1] = vfma(r.omw[5], D[1][0][1], r.nw[5] * (ux * uz));
+    D[0][1][1] = vfma(r.omw[6], D[0][1][1], r.nw[6] * (uy * uz));
 
     // order 2, diagonal: xx-yy -> 0, xx+yy-2zz -> 0, xx+yy+zz -> rho
     {
-        float a = D[2][0][0] - D[0][2][0];
-        float b = D[2][0][0] + D[0][2][0] - 2.0f * D[0][0][2];
-        float c = D[2][0][0] + D[0][2][0] + D[0][0][2];
-        a = fmaf(1.0f - r.w[7], a, -r.w[7] * (ux2 - uy2));
-        b = fmaf(1.0f - r.w[8], b, -r.w[8] * (ux2 + uy2 - 2.0f * uz2));
-        c = fmaf(1.0f - r.w[9], c, r.w[9] * (drho - (ux2 + uy2 + uz2)));
-        const float c3 = c * third, b6 = b * (1.0f / 6.0f);
-        D[2][0][0] = c3 + b6 + 0.5f * a;
-        D[0][2][0] = c3 + b6 - 0.5f * a;
-        D[0][0][2] = c3 - 2.0f * b6;
+        const V xy = D[2][0][0] + D[0][2][0];
+        V a = D[2][0][0] - D[0][2][0];
+        V b = xy - two * D[0][0][2];
+        V c = xy + D[0][0][2];
+        const V uxy = ux2 + uy2;
+        a = vfma(r.omw[7], a, r.nw[7] * (ux2 - uy2));
+        b = vfma(r.omw[8], b, r.nw[8] * (uxy - two * uz2));
+        c = vfma(r.omw[9], c, r.w[9] * (drho - (uxy + uz2)));
+        const V c3 = c * third, b6 = b * sixth;
+        const V cb = c3 + b6;
+        D[2][0][0] = vfma(half, a, cb);
+        D[0][2][0] = cb - half * a;
+        D[0][0][2] = c3 - two * b6;
     }
-    const float dxx = D[2][0][0], dyy = D[0][2][0], dzz = D[0][0][2];  // post-collision
+    const V dxx = D[2][0][0], dyy = D[0][2][0], dzz = D[0][0][2];  // post-collision
 
     // order 3: attractors 0; kappa^w_xyy = -u_x Kw_y etc.
     {
-        float s = D[1][2][0] + D[1][0][2], t = D[1][2][0] - D[1][0][2];
-        s = fmaf(1.0f - r.w[10], s, r.w[10] * ux * (Kwy + Kwz));
-        t = fmaf(1.0f - r.w[13], t, r.w[13] * ux * (Kwy - Kwz));
-        D[1][2][0] = 0.5f * (s + t);
-        D[1][0][2] = 0.5f * (s - t);
+        const V s = D[1][2][0] + D[1][0][2], t = D[1][2][0] - D[1][0][2];
+        const V sn = vfma(r.omw[10], s, r.w[10] * (ux * (Kwy + Kwz)));
+        const V tn = vfma(r.omw[13], t, r.w[13] * (ux * (Kwy - Kwz)));
+        D[1][2][0] = half * (sn + tn);
+        D[1][0][2] = half * (sn - tn);
     }
     {
-        float s = D[2][1][0] + D[0][1][2], t = D[2][1][0] - D[0][1][2];
-        s = fmaf(1.0f - r.w[11], s, r.w[11] * uy * (Kwx + Kwz));
-        t = fmaf(1.0f - r.w[14], t, r.w[14] * uy * (Kwx - Kwz));
-        D[2][1][0] = 0.5f * (s + t);
-        D[0][1][2] = 0.5f * (s - t);
+        const V s = D[2][1][0] + D[0][1][2], t = D[2][1][0] - D[0][1][2];
+        const V sn = vfma(r.omw[11], s, r.w[11] * (uy * (Kwx + Kwz)));
+        const V tn = vfma(r.omw[14], t, r.w[14] * (uy * (Kwx - Kwz)));
+        D[2][1][0] = half * (sn + tn);
+        D[0][1][2] = half * (sn - tn);
     }
     {
-        float s = D[2][0][1] + D[0][2][1], t = D[2][0][1] - D[0][2][1];
-        s = fmaf(1.0f - r.w[12], s, r.w[12] * uz * (Kwx + Kwy));
-        t = fmaf(1.0f - r.w[15], t, r.w[15] * uz * (Kwx - Kwy));
-        D[2][0][1] = 0.5f * (s + t);
-        D[0][2][1] = 0.5f * (s - t);
+        const V s = D[2][0][1] + D[0][2][1], t = D[2][0][1] - D[0][2][1];
+        const V sn = vfma(r.omw[12], s, r.w[12] * (uz * (Kwx + Kwy)));
+        const V tn = vfma(r.omw[15], t, r.w[15] * (uz * (Kwx - Kwy)));
+        D[2][0][1] = half * (sn + tn);
+        D[0][2][1] = half * (sn - tn);
     }
-    D[1][1][1] = fmaf(1.0f - r.w[16], D[1][1][1], r.w[16] * ux * uy * uz);
+    D[1][1][1] = vfma(r.omw[16], D[1][1][1], r.w[16] * (ux * uy * uz));
 
     // order 4: xxyy, xxzz, yyzz -> products of the post-collision kappa~_ii
     {
-        const float dA = fmaf(Kwx, dyy, fmaf(Kwy, dxx, dxx * dyy));  // kt_x kt_y - Kw_x Kw_y
-        const float dB = fmaf(Kwx, dzz, fmaf(Kwz, dxx, dxx * dzz));
-        const float dC = fmaf(Kwy, dzz, fmaf(Kwz, dyy, dyy * dzz));
-        const float A = D[2][2][0], B = D[2][0][2], C = D[0][2][2];
-        float p17 = A + B + C, p18 = A + B - 2.0f * C, p19 = A - B;
-        p17 = fmaf(1.0f - r.w[17], p17, r.w[17] * (dA + dB + dC));
-        p18 = fmaf(1.0f - r.w[18], p18, r.w[18] * (dA + dB - 2.0f * dC));
-        p19 = fmaf(1.0f - r.w[19], p19, r.w[19] * (dA - dB));
-        const float Cn = (p17 - p18) * third;
-        const float ABn = (2.0f * p17 + p18) * third;
-        D[2][2][0] = 0.5f * (ABn + p19);
-        D[2][0][2] = 0.5f * (ABn - p19);
-        D[0][2][2] = Cn;
+        const V dA = vfma(Kwx, dyy, vfma(Kwy, dxx, dxx * dyy));  // kt_x kt_y - Kw_x Kw_y
+        const V dB = vfma(Kwx, dzz, vfma(Kwz, dxx, dxx * dzz));
+        const V dC = vfma(Kwy, dzz, vfma(Kwz, dyy, dyy * dzz));
+        const V A = D[2][2][0], B = D[2][0][2], C = D[0][2][2];
+        const V AB = A + B, dAB = dA + dB;
+        const V p17 = vfma(r.omw[17], AB + C, r.w[17] * (dAB + dC));
+        const V p18 = vfma(r.omw[18], AB - two * C, r.w[18] * (dAB - two * dC));
+        const V p19 = vfma(r.omw[19], A - B, r.w[19] * (dA - dB));
+        const V ABn = third * (two * p17 + p18);
+        D[0][2][2] = third * (p17 - p18);
+        D[2][2][0] = half * (ABn + p19);
+        D[2][0][2] = half * (ABn - p19);
     }
     // xxyz, xyyz, xyzz -> 0; kappa^w_xxyz = Kw_x u_y u_z etc.
-    D[2][1][1] = fmaf(1.0f - r.w[20], D[2][1][1], -r.w[20] * Kwx * uy * uz);
-    D[1][2][1] = fmaf(1.0f - r.w[21], D[1][2][1], -r.w[21] * ux * Kwy * uz);
-    D[1][1][2] = fmaf(1.0f - r.w[22], D[1][1][2], -r.w[22] * ux * uy * Kwz);
+    D[2][1][1] = vfma(r.omw[20], D[2][1][1], r.nw[20] * (Kwx * (uy * uz)));
+    D[1][2][1] = vfma(r.omw[21], D[1][2][1], r.nw[21] * (Kwy * (ux * uz)));
+    D[1][1][2] = vfma(r.omw[22], D[1][1][2], r.nw[22] * (Kwz * (ux * uy)));
 
     // order 5 -> 0; kappa^w_xyyzz = -u_x Kw_y Kw_z etc.
-    D[1][2][2] = fmaf(1.0f - r.w[23], D[1][2][2], r.w[23] * ux * Kwy * Kwz);
-    D[2][1][2] = fmaf(1.0f - r.w[24], D[2][1][2], r.w[24] * uy * Kwx * Kwz);
-    D[2][2][1] = fmaf(1.0f - r.w[25], D[2][2][1], r.w[25] * uz * Kwx * Kwy);
+    D[1][2][2] = vfma(r.omw[23], D[1][2][2], r.w[23] * (ux * (Kwy * Kwz)));
+    D[2][1][2] = vfma(r.omw[24], D[2][1][2], r.w[24] * (uy * (Kwx * Kwz)));
+    D[2][2][1] = vfma(r.omw[25], D[2][2][1], r.w[25] * (uz * (Kwx * Kwy)));
 
-    // order 6: xxyyzz -> kt_x kt_y kt_z
+    // order 6: xxyyzz -> kt_x kt_y kt_z;  kt_x kt_y kt_z - Kw_x Kw_y Kw_z
     {
-        const float dK = dxx * Kwy * Kwz + dyy * Kwx * Kwz + dzz * Kwx * Kwy +
-                         dxx * dyy * Kwz + dxx * dzz * Kwy + dyy * dzz * Kwx + dxx * dyy * dzz;
-        D[2][2][2] = fmaf(1.0f - r.w[26], D[2][2][2], r.w[26] * dK);
+        const V ktx = Kwx + dxx, kty = Kwy + dyy;
+        // (Kwx + dxx)(Kwy + dyy)(Kwz + dzz) - Kwx Kwy Kwz
+        //   = kt_x kt_y dzz + Kwz (kt_x dyy + Kwy dxx)
+        const V dK = vfma(ktx * kty, dzz, Kwz * vfma(ktx, dyy, Kwy * dxx));
+        D[2][2][2] = vfma(r.omw[26], D[2][2][2], r.w[26] * dK);
     }
 }
 
-// Forward transform of deviations f[slot] into raw-sum / central-moment
-// space.  Returns drho, j and u; D holds the central moments about u of the
+// Forward transform of deviations f[slot] into central-moment space.
+// Returns drho and u; D holds the central moments about u of the
 // deviations, to which the caller adds the source.
-__device__ __forceinline__ void forward27(const float (&f)[27], float (&D)[3][3][3], float Fx,
-                                          float Fy, float Fz, float &drho, float &ux, float &uy,
-                                          float &uz) {
-    // x: raw sums of each (y, z) line
+template <typename V>
+__device__ __forceinline__ void forward27(const V (&f)[27], V (&D)[3][3][3], V Fx, V Fy, V Fz,
+                                          V &drho, V &ux, V &uy, V &uz) {
+    // raw sums along x, then y, then z
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
         for (int k = 0; k < 3; ++k)
             sums(f[s27(0, j, k)], f[s27(1, j, k)], f[s27(2, j, k)], D[0][j][k], D[1][j][k],
                  D[2][j][k]);
-    // y: raw sums over y of each x-moment line
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            float s0, s1, s2;
+            V s0, s1, s2;
             sums(D[m][0][k], D[m][1][k], D[m][2][k], s0, s1, s2);
             D[m][0][k] = s0;
             D[m][1][k] = s1;
             D[m][2][k] = s2;
         }
-    // z
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
         for (int n = 0; n < 3; ++n) {
-            float s0, s1, s2;
+            V s0, s1, s2;
             sums(D[m][n][0], D[m][n][1], D[m][n][2], s0, s1, s2);
             D[m][n][0] = s0;
             D[m][n][1] = s1;
             D[m][n][2] = s2;
         }
     // D now holds raw moments of the deviations; the rest state has raw
-    // moments (1, 0, 1/3, ...) which sum to rho = 1 + drho, j = j_dev.
+    // moments (1, 0, 1/3, ...), so rho = 1 + drho and j = j_dev.
+    const V half = splat<V>(0.5f);
     drho = D[0][0][0];
-    const float inv_rho = 1.0f / (1.0f + drho);
-    ux = (D[1][0][0] + 0.5f * Fx) * inv_rho;
-    uy = (D[0][1][0] + 0.5f * Fy) * inv_rho;
-    uz = (D[0][0][1] + 0.5f * Fz) * inv_rho;
+    const V inv_rho = vrcp(splat<V>(1.0f) + drho);
+    ux = vfma(half, Fx, D[1][0][0]) * inv_rho;
+    uy = vfma(half, Fy, D[0][1][0]) * inv_rho;
+    uz = vfma(half, Fz, D[0][0][1]) * inv_rho;
+    const V zero = splat<V>(0.0f);
+    const V nux = zero - ux, nuy = zero - uy, nuz = zero - uz;
     // shift raw -> central about u, one axis at a time (the shifts commute)
 #pragma unroll
     for (int n = 0; n < 3; ++n)
 #pragma unroll
-        for (int p = 0; p < 3; ++p) central_from_sums(ux, D[0][n][p], D[1][n][p], D[2][n][p]);
+        for (int p = 0; p < 3; ++p) central_from_sums(nux, D[0][n][p], D[1][n][p], D[2][n][p]);
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
-        for (int p = 0; p < 3; ++p) central_from_sums(uy, D[m][0][p], D[m][1][p], D[m][2][p]);
+        for (int p = 0; p < 3; ++p) central_from_sums(nuy, D[m][0][p], D[m][1][p], D[m][2][p]);
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
-        for (int n = 0; n < 3; ++n) central_from_sums(uz, D[m][n][0], D[m][n][1], D[m][n][2]);
+        for (int n = 0; n < 3; ++n) central_from_sums(nuz, D[m][n][0], D[m][n][1], D[m][n][2]);
 }
 
 // Inverse transform: deviation central moments about u -> deviations f[slot].
-__device__ __forceinline__ void inverse27(float (&D)[3][3][3], float ux, float uy, float uz,
-                                          float (&f)[27]) {
+template <typename V>
+__device__ __forceinline__ void inverse27(V (&D)[3][3][3], V ux, V uy, V uz, V (&f)[27]) {
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
         for (int n = 0; n < 3; ++n) {
-            float a, b, c;
+            V a, b, c;
             dist_from_central(uz, D[m][n][0], D[m][n][1], D[m][n][2], a, b, c);
             D[m][n][0] = a;
             D[m][n][1] = b;
@@ -227,7 +245,7 @@ __device__ __forceinline__ void inverse27(float (&D)[3][3][3], float ux, float u
     for (int m = 0; m < 3; ++m)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            float a, b, c;
+            V a, b, c;
             dist_from_central(uy, D[m][0][k], D[m][1][k], D[m][2][k], a, b, c);
             D[m][0][k] = a;
             D[m][1][k] = b;
@@ -241,21 +259,20 @@ __device__ __forceinline__ void inverse27(float (&D)[3][3][3], float ux, float u
                               f[s27(1, j, k)], f[s27(2, j, k)]);
 }
 
-// One cell: pre-collision deviations in, post-collision deviations out
-// (both f - w, slot order).  (Fx, Fy, Fz): the cell's body force.
-__device__ __forceinline__ void collide27(float (&f)[27], float Fx, float Fy, float Fz,
-                                          const RelaxRates27 &r) {
-    float D[3][3][3];
-    float drho, ux, uy, uz;
+// One cell (or a pair of cells, V = f2): pre-collision deviations in,
+// post-collision deviations out (both f - w, slot order).
+template <typename V>
+__device__ __forceinline__ void collide27(V (&f)[27], V Fx, V Fy, V Fz, const Rates27<V> &r) {
+    V D[3][3][3];
+    V drho, ux, uy, uz;
     forward27(f, D, Fx, Fy, Fz, drho, ux, uy, uz);
-    // central moments of the source: F at first order (Eq. discretecentralsources)
-    D[1][0][0] += Fx;
-    D[0][1][0] += Fy;
-    D[0][0][1] += Fz;
-    // d = kappa - kappa^w: the rest state's central moments about u are
-    // k_m(u_x) k_n(u_y) k_p(u_z), with deviations counted from them.  The
-    // forward sweep produced central moments of the deviations, i.e. d
-    // already (kappa^w is the part carried by w itself).
+    // The sweeps produced the central moments of the deviations; those of
+    // the rest state are handled in closed form inside relax27, so D is
+    // d = kappa - kappa^w.  Add the source's central moments: F at first
+    // order, zero elsewhere (Eq. discretecentralsources).
+    D[1][0][0] = D[1][0][0] + Fx;
+    D[0][1][0] = D[0][1][0] + Fy;
+    D[0][0][1] = D[0][0][1] + Fz;
     relax27(D, ux, uy, uz, drho, r);
     inverse27(D, ux, uy, uz, f);
 }
@@ -300,7 +317,7 @@ __device__ __forceinline__ void equilibrium27(float drho, float ux, float uy, fl
     D[2][2][1] = uz * Kwx * Kwy;
     D[2][2][2] = dx * Kwy * Kwz + dy * Kwx * Kwz + dz * Kwx * Kwy + dx * dy * Kwz +
                  dx * dz * Kwy + dy * dz * Kwx + dx * dy * dz;
-    inverse27(D, ux, uy, uz, f);
+    inverse27<float>(D, ux, uy, uz, f);
 }
 
 }  // namespace lbm

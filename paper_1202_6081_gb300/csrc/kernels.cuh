@@ -6,6 +6,9 @@
 #include "collide_q15.cuh"
 #include "collide_q27.cuh"
 #include "lattice.cuh"
+#include "vec2.cuh"
+
+#include <cstring>
 
 namespace lbm {
 
@@ -48,18 +51,35 @@ template <int Q>
 struct Rates;
 template <>
 struct Rates<27> {
-    using type = RelaxRates27;
+    using type = Rates27<float>;
 };
 template <>
 struct Rates<15> {
     using type = RelaxRates15;
 };
 
-template <int Q>
-__device__ __forceinline__ typename Rates<Q>::type load_rates(const StepArgs &a) {
-    typename Rates<Q>::type r;
+__device__ __forceinline__ Rates27<float> load_rates27(const StepArgs &a) {
+    Rates27<float> r;
 #pragma unroll
-    for (int b = 0; b < Q; ++b) r.w[b] = a.w[b];
+    for (int b = 0; b < 27; ++b) {
+        r.w[b] = a.w[b];
+        r.nw[b] = -a.w[b];
+        r.omw[b] = 1.0f - a.w[b];
+    }
+    return r;
+}
+
+template <int Q>
+__device__ __forceinline__ typename Rates<Q>::type load_rates(const StepArgs &a);
+template <>
+__device__ __forceinline__ Rates27<float> load_rates<27>(const StepArgs &a) {
+    return load_rates27(a);
+}
+template <>
+__device__ __forceinline__ RelaxRates15 load_rates<15>(const StepArgs &a) {
+    RelaxRates15 r;
+#pragma unroll
+    for (int b = 0; b < 15; ++b) r.w[b] = a.w[b];
     return r;
 }
 
@@ -68,8 +88,8 @@ __device__ __forceinline__ void collide(float (&f)[Q], float Fx, float Fy, float
                                         const typename Rates<Q>::type &r);
 template <>
 __device__ __forceinline__ void collide<27>(float (&f)[27], float Fx, float Fy, float Fz,
-                                            const RelaxRates27 &r) {
-    collide27(f, Fx, Fy, Fz, r);
+                                            const Rates27<float> &r) {
+    collide27<float>(f, Fx, Fy, Fz, r);
 }
 template <>
 __device__ __forceinline__ void collide<15>(float (&f)[15], float Fx, float Fy, float Fz,
@@ -104,21 +124,186 @@ __device__ __forceinline__ void cell_force(const StepArgs &a, long long c, long 
     }
 }
 
-// One fused step: pull-gather (streaming with bounce-back), collision, store.
-template <int Q, typename T>
-__global__ void __launch_bounds__(128) step_kernel(const T *__restrict__ fin,
-                                                   T *__restrict__ fout, const StepArgs a) {
+// Base pointer of every population plane of the source and destination
+// buffers (plane alpha starts at buf + alpha * pop).  Passed by value, the
+// table sits in the constant bank, so each access is one multiply-add of a
+// 32-bit element offset onto a constant-bank base.
+template <typename T>
+struct StepIO {
+    const T *in[27];
+    T *out[27];
+};
+
+// 2-cell pair helpers for the packed kernel (x0 even, row pitch even).
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    __device__ __forceinline__ static f2 ld2(const float *p) {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        return f2(v.x, v.y);
+    }
+    __device__ __forceinline__ static float ld1(const float *p) { return __ldg(p); }
+    __device__ __forceinline__ static void st2(float *p, f2 v) {
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(v.lo(), v.hi()));
+    }
+};
+template <>
+struct Pair<__half> {
+    __device__ __forceinline__ static f2 ld2(const __half *p) {
+        const float2 v = __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
+        return f2(v.x, v.y);
+    }
+    __device__ __forceinline__ static float ld1(const __half *p) {
+        return __half2float(__ldg(p));
+    }
+    __device__ __forceinline__ static void st2(__half *p, f2 v) {
+        const __half2 h = __floats2half2_rn(v.lo(), v.hi());
+        __stcs(reinterpret_cast<unsigned int *>(p), *reinterpret_cast<const unsigned int *>(&h));
+    }
+};
+template <>
+struct Pair<__nv_bfloat16> {
+    __device__ __forceinline__ static f2 ld2(const __nv_bfloat16 *p) {
+        const float2 v = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
+        return f2(v.x, v.y);
+    }
+    __device__ __forceinline__ static float ld1(const __nv_bfloat16 *p) {
+        return __bfloat162float(__ldg(p));
+    }
+    __device__ __forceinline__ static void st2(__nv_bfloat16 *p, f2 v) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.lo(), v.hi());
+        __stcs(reinterpret_cast<unsigned int *>(p), *reinterpret_cast<const unsigned int *>(&h));
+    }
+};
+
+// Relaxation rates pre-broadcast to both lanes, built on the host.
+struct PackedRates {
+    unsigned long long w[27], nw[27], omw[27];
+};
+
+__device__ __forceinline__ Rates27<f2> load_rates_packed(const PackedRates &p) {
+    Rates27<f2> r;
+#pragma unroll
+    for (int b = 0; b < 27; ++b) {
+        r.w[b] = f2(p.w[b]);
+        r.nw[b] = f2(p.nw[b]);
+        r.omw[b] = f2(p.omw[b]);
+    }
+    return r;
+}
+
+// Row offsets (elements) of the 3 x 3 source rows of a pull, for cell row
+// (y, z); wall[j][k] set where that source is beyond a bounce-back wall.
+template <bool kWalls>
+struct Rows {
+    int off[3][3];
+    bool wall[3][3];
+    int own;
+};
+
+template <bool kWalls>
+__device__ __forceinline__ Rows<kWalls> pull_rows(const Grid &g, int y, int z) {
+    Rows<kWalls> r;
+    const int ys[3] = {(y + 1 == g.ny) ? 0 : y + 1, y, (y == 0) ? g.ny - 1 : y - 1};
+    const int zs[3] = {(z + 1 == g.nz) ? 0 : z + 1, z, (z == 0) ? g.nz - 1 : z - 1};
+    bool wy[3] = {false, false, false}, wz[3] = {false, false, false};
+    if (kWalls) {
+        wy[0] = (y + 1 == g.ny) && (g.bc & kWallY);
+        wy[2] = (y == 0) && (g.bc & kWallY);
+        wz[0] = (z + 1 == g.nz) && (g.bc & kWallZ);
+        wz[2] = (z == 0) && (g.bc & kWallZ);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            r.off[j][k] = (zs[k] * g.ny + ys[j]) * g.px;
+            r.wall[j][k] = kWalls && (wy[j] || wz[k]);
+        }
+    r.own = (z * g.ny + y) * g.px;
+    return r;
+}
+
+// One fused step, one cell per thread: pull-gather (streaming with
+// bounce-back), collision, store.
+template <int Q, typename T, bool kWalls>
+__global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const StepArgs a) {
     int x, y, z;
     if (!cell_coords(a.g, x, y, z)) return;
-    const PullSources s = pull_sources(a.g, x, y, z);
+    const Rows<kWalls> R = pull_rows<kWalls>(a.g, y, z);
+    const int xs[3] = {(x + 1 == a.g.nx) ? 0 : x + 1, x, (x == 0) ? a.g.nx - 1 : x - 1};
     float f[Q];
-    gather<Q, T>(fin, a.g, s, f);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int i = ex<Q>(q) + 1, j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
+        float v;
+        if (kWalls && R.wall[j][k])
+            v = Storage<T>::load(io.in[opposite<Q>(q)] + R.own + x);
+        else
+            v = Storage<T>::load(io.in[q] + R.off[j][k] + xs[i]);
+        f[q] = Storage<T>::kScaled ? v * float(weight<Q>(q)) : v;
+    }
     float Fx, Fy, Fz;
     const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
     cell_force(a, dense_index(a.g, x, y, z), N, Fx, Fy, Fz);
     const typename Rates<Q>::type r = load_rates<Q>(a);
     collide<Q>(f, Fx, Fy, Fz, r);
-    store_own<Q, T>(fout, a.g, s.own, f);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) store_dev<Q, T>(io.out[q] + R.own + x, q, f[q]);
+}
+
+// One fused D3Q27 step, two neighbouring cells (x0, x0 + 1) per thread with
+// the collision in packed f32x2 arithmetic.  nx must be even.  Loads of
+// populations with e_x = 0 and all stores are aligned 2-element accesses;
+// e_x = +-1 sources are two single loads (x0 - 1, x0) or (x0 + 1, x0 + 2).
+template <typename T, bool kWalls>
+__global__ void __launch_bounds__(128) step2_kernel(const StepIO<T> io, const StepArgs a,
+                                                    const PackedRates pr) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    const int x0 = 2 * t;
+    if (x0 >= a.g.nx || y >= a.g.ny) return;
+    const Rows<kWalls> R = pull_rows<kWalls>(a.g, y, z);
+    const int xm = (x0 == 0) ? a.g.nx - 1 : x0 - 1;
+    const int xp = (x0 + 2 == a.g.nx) ? 0 : x0 + 2;
+    f2 f[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        const int i = ex<27>(q), j = ey<27>(q) + 1, k = ez<27>(q) + 1;
+        f2 v;
+        if (kWalls && R.wall[j][k]) {
+            v = Pair<T>::ld2(io.in[opposite<27>(q)] + R.own + x0);
+        } else {
+            const T *row = io.in[q] + R.off[j][k];
+            if (i == 0)
+                v = Pair<T>::ld2(row + x0);
+            else if (i == 1)
+                v = f2(Pair<T>::ld1(row + xm), Pair<T>::ld1(row + x0));
+            else
+                v = f2(Pair<T>::ld1(row + x0 + 1), Pair<T>::ld1(row + xp));
+        }
+        f[q] = Storage<T>::kScaled ? v * f2(float(weight<27>(q))) : v;
+    }
+    f2 Fx, Fy, Fz;
+    if (a.Ffield) {
+        const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
+        const long long c = dense_index(a.g, x0, y, z);
+        Fx = f2(__ldg(a.Ffield + c), __ldg(a.Ffield + c + 1));
+        Fy = f2(__ldg(a.Ffield + N + c), __ldg(a.Ffield + N + c + 1));
+        Fz = f2(__ldg(a.Ffield + 2 * N + c), __ldg(a.Ffield + 2 * N + c + 1));
+    } else {
+        Fx = f2(a.F[0]);
+        Fy = f2(a.F[1]);
+        Fz = f2(a.F[2]);
+    }
+    const Rates27<f2> r = load_rates_packed(pr);
+    collide27<f2>(f, Fx, Fy, Fz, r);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<27>(q))) : f[q];
+        Pair<T>::st2(io.out[q] + R.own + x0, v);
+    }
 }
 
 // Initial state from FP64 density and velocity fields.
@@ -205,27 +390,31 @@ __global__ void __launch_bounds__(128) macro_kernel(const T *__restrict__ buf, c
 constexpr int kRedThreads = 256;
 constexpr int kRedMaxBlocks = 2048;
 
-// Partial sums of (rho - 1, rho u) per block in FP64, fixed order.
+// Partial sums of (rho - 1, rho u) per block, fixed order.  Each block takes
+// whole (y, z) rows (row = blockIdx.x + k * gridDim.x) and its threads stride
+// along x, so cells are decoded with one division per row.  A cell's moments
+// are FP32 sums of its 27 (15) stored deviations; the running sums across
+// cells are FP64 (FP64 is slow on this GPU, so it is kept to 4 adds per cell).
 template <int Q, typename T>
 __global__ void __launch_bounds__(kRedThreads) conservation_kernel(const T *__restrict__ buf,
                                                                    const StepArgs a,
                                                                    double *__restrict__ part) {
     const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
+    const long long rows = (long long)a.g.ny * a.g.nz;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int x = int(c % a.g.nx);
-        const long long yz = c / a.g.nx;
-        const int y = int(yz % a.g.ny), z = int(yz / a.g.ny);
-        float f[Q];
-        gather<Q, T>(buf, a.g, pull_sources(a.g, x, y, z), f);
-        float drho, jx, jy, jz, Fx, Fy, Fz;
-        moments<Q>(f, drho, jx, jy, jz);
-        cell_force(a, c, N, Fx, Fy, Fz);
-        acc[0] += drho;
-        acc[1] += double(jx) + 0.5 * Fx;
-        acc[2] += double(jy) + 0.5 * Fy;
-        acc[3] += double(jz) + 0.5 * Fz;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int y = int(row % a.g.ny), z = int(row / a.g.ny);
+        for (int x = threadIdx.x; x < a.g.nx; x += blockDim.x) {
+            float f[Q];
+            gather<Q, T>(buf, a.g, pull_sources(a.g, x, y, z), f);
+            float drho, jx, jy, jz, Fx, Fy, Fz;
+            moments<Q>(f, drho, jx, jy, jz);
+            cell_force(a, row * a.g.nx + x, N, Fx, Fy, Fz);
+            acc[0] += double(drho);
+            acc[1] += double(jx + 0.5f * Fx);
+            acc[2] += double(jy + 0.5f * Fy);
+            acc[3] += double(jz + 0.5f * Fz);
+        }
     }
     __shared__ double sh[4][kRedThreads];
 #pragma unroll
@@ -244,11 +433,51 @@ __global__ void __launch_bounds__(kRedThreads) conservation_kernel(const T *__re
 
 // Launchers.  kernels_q27.cu / kernels_q15.cu hold their explicit
 // instantiations; api.cu sees them through the extern declarations below.
+inline PackedRates packed_rates(const StepArgs &a) {
+    PackedRates p;
+    for (int b = 0; b < 27; ++b) {
+        const float w = a.w[b], nw = -a.w[b], omw = 1.0f - a.w[b];
+        unsigned int uw, unw, uomw;
+        memcpy(&uw, &w, 4);
+        memcpy(&unw, &nw, 4);
+        memcpy(&uomw, &omw, 4);
+        p.w[b] = (unsigned long long)uw << 32 | uw;
+        p.nw[b] = (unsigned long long)unw << 32 | unw;
+        p.omw[b] = (unsigned long long)uomw << 32 | uomw;
+    }
+    return p;
+}
+
+// The packed two-cells-per-thread kernel serves D3Q27 grids with even nx;
+// every other grid takes the one-cell kernel.
 template <int Q, typename T>
 cudaError_t launch_step(const void *fin, void *fout, const StepArgs &a, cudaStream_t st) {
-    const CellLaunch L = cell_launch(a.g);
-    step_kernel<Q, T><<<L.grid, L.block, 0, st>>>(static_cast<const T *>(fin),
-                                                  static_cast<T *>(fout), a);
+    StepIO<T> io;
+    for (int q = 0; q < 27; ++q) {
+        io.in[q] = static_cast<const T *>(fin) + (q < Q ? q * a.g.pop : 0);
+        io.out[q] = static_cast<T *>(fout) + (q < Q ? q * a.g.pop : 0);
+    }
+    const bool walls = a.g.bc != 0;
+    if constexpr (Q == 27) {
+        if (a.g.nx % 2 == 0) {
+            Grid half = a.g;
+            half.nx = a.g.nx / 2;
+            const CellLaunch L = cell_launch(half);
+            const PackedRates pr = packed_rates(a);
+            if (walls)
+                step2_kernel<T, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+            else
+                step2_kernel<T, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
+            return cudaGetLastError();
+        }
+    }
+    {
+        const CellLaunch L = cell_launch(a.g);
+        if (walls)
+            step_kernel<Q, T, true><<<L.grid, L.block, 0, st>>>(io, a);
+        else
+            step_kernel<Q, T, false><<<L.grid, L.block, 0, st>>>(io, a);
+    }
     return cudaGetLastError();
 }
 
@@ -293,9 +522,10 @@ cudaError_t launch_conservation(const void *buf, const StepArgs &a, double *part
 // Final reduction of the per-block partials to 4 doubles (one block).
 cudaError_t launch_reduce_final(const double *part, int blocks, double *out, cudaStream_t st);
 
-// Number of partial-sum blocks the conservation reduction uses for N cells.
-inline int conservation_blocks(long long N) {
-    long long b = (N + kRedThreads - 1) / kRedThreads;
+// Number of partial-sum blocks the conservation reduction uses: one per
+// (y, z) row up to kRedMaxBlocks.
+inline int conservation_blocks(const Grid &g) {
+    long long b = (long long)g.ny * g.nz;
     if (b > kRedMaxBlocks) b = kRedMaxBlocks;
     if (b < 1) b = 1;
     return int(b);

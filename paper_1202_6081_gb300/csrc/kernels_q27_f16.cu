@@ -1,0 +1,6 @@
+// Explicit instantiation of the D3Q27 kernels with F16 storage.
+#include "kernels.cuh"
+
+namespace lbm {
+LBM_INSTANTIATE_1(, 27, __half)
+}  // namespace lbm
