@@ -298,6 +298,57 @@ def e2e_job(torch, lbm, size, steps):
                    "rho,u (FP32)" % steps}
 
 
+def adjoint_timing(torch, lbm, size, steps=100):
+    """Adjoint step vs forward step at the adjoint workload (D3Q27, size^3
+    periodic, tau = 0.6, per-cell force field), both by CUDA events; plus a
+    whole checkpointed gradient (200 steps, checkpoint every 20)."""
+    import workloads as W
+    from paper_1202_6081_gb300.autograd import kinetic_energy_after
+    Q = 27
+    shape = (size, size, size)
+    om = W.omegas(Q, 1 / 0.6)
+    rho, u = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    F = torch.as_tensor(W.gaussian_force_field(shape, rms=1e-5, sigma=4.0).astype(np.float32),
+                        device="cuda").contiguous()
+    S = lbm.Solver(Q, shape, om)
+    S.set_force_field(F)
+    S.init_equilibrium(rho, u)
+    t_fwd = time_steps(torch, S, steps, 5) / steps
+    f_t = S.current_buffer()
+    lam = [S.new_adjoint_field(), S.new_adjoint_field()]
+    gF = torch.zeros_like(F)
+    stream = torch.cuda.current_stream()
+    for i in range(5):
+        S.adjoint_step(f_t, lam[i % 2], lam[1 - i % 2], gF)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        S.adjoint_step(f_t, lam[i % 2], lam[1 - i % 2], gF)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_adj = e0.elapsed_time(e1) / 1e3 / steps
+    cells = size**3
+    # whole gradient: forward with checkpoints, then backward (recompute + adjoint)
+    Fg = F.clone().requires_grad_()
+    init = S.current_buffer().clone()
+    S.load_buffer(init)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = kinetic_energy_after(S, Fg, 200, 20)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"workload": "D3Q27 %d^3 periodic, tau=0.6, force field, FP32" % size,
+            "forward_ms_per_step": t_fwd * 1e3, "adjoint_ms_per_step": t_adj * 1e3,
+            "adjoint_forward_ratio": t_adj / t_fwd,
+            "adjoint_GB/s": 360 * cells / t_adj / 1e9,
+            "gradient_200_steps": {"forward_s": t1 - t0, "backward_s": t2 - t1,
+                                   "backward_forward_ratio": (t2 - t1) / (t1 - t0)}}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -371,6 +422,8 @@ def run_ours(args):
             del S
             torch.cuda.empty_cache()
         result["storage_512"] = s16
+        result["adjoint"] = adjoint_timing(torch, lbm, 128)
+        torch.cuda.empty_cache()
         result["cpu_baseline"] = cpu_baseline(size)
     if rank == 0:
         print(json.dumps(result), flush=True)

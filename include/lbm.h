@@ -116,6 +116,10 @@ lbm_status lbm_bind(lbm_ctx *ctx, void *f_a, void *f_b, const float *force_field
  * enqueued after this call (the value is passed by argument to each launch). */
 lbm_status lbm_set_force(lbm_ctx *ctx, const double *force);
 
+/* Replace the per-cell force field (device FP32 [3][nz][ny][nx]; NULL = use
+ * the uniform force) for work enqueued after this call; the state is kept. */
+lbm_status lbm_set_force_field(lbm_ctx *ctx, const float *force_field);
+
 /* Replace the relaxation rates (host, Q values, as in lbm_create). */
 lbm_status lbm_set_omega(lbm_ctx *ctx, const double *omega);
 
@@ -155,6 +159,50 @@ lbm_status lbm_macroscopic(const lbm_ctx *ctx, float *rho, float *u, void *strea
  * Errors: LBM_ESTATE, LBM_ENOMEM (scratch), LBM_ECUDA, LBM_ENONFINITE (out is
  * still written). */
 lbm_status lbm_conservation(lbm_ctx *ctx, double out[4], void *stream);
+
+/* ---- discrete adjoint (D3Q27; not in the paper: the reverse mode of its
+ * update, for gradients with respect to a per-cell body force) ---------- */
+
+/* Size in bytes of one adjoint field lam: FP32, laid out like an FP32 state
+ * buffer (Q population planes of pitched rows; see lbm_state_bytes). */
+size_t lbm_adjoint_bytes(const lbm_ctx *ctx);
+
+/* The bound buffer that holds the current state (NULL before a state is
+ * set).  Valid until the next lbm_step / lbm_bind; lets a caller checkpoint
+ * the state with a device-to-device copy of lbm_state_bytes. */
+const void *lbm_current_state(const lbm_ctx *ctx);
+
+/* One collide-and-stream step from the state in f_in to f_out (device,
+ * lbm_state_bytes each, 256-byte aligned, not overlapping; any buffers, not
+ * only the bound pair, e.g. a checkpoint ring).  The bound pair and the
+ * current state are untouched.  Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_step_into(lbm_ctx *ctx, const void *f_in, void *f_out, void *stream);
+
+/* Adjoint of one step taken from the state f_t (a state buffer holding the
+ * state at time t):
+ *     lam_out(y) = J_C(f_t(y))^T mu(y),  mu_a(y) = lam_next_a(y + e_a)
+ * (lam_next_opp(a)(y) where y + e_a is behind a bounce-back wall), J_C the
+ * per-cell Jacobian of the collision, and, when dJdF is not NULL,
+ *     dJdF(y) += (dC/dF(y))^T mu(y)
+ * (device FP32 [3][nz][ny][nx], accumulated; the force of step t is the
+ * bound force field or the uniform force).  lam_next, lam_out: device FP32
+ * adjoint fields (lbm_adjoint_bytes, 16-byte aligned, distinct).
+ * Errors: LBM_EINVAL, LBM_EUNSUPPORTED (D3Q15), LBM_ECUDA. */
+lbm_status lbm_adjoint_step(lbm_ctx *ctx, const void *f_t, const float *lam_next,
+                            float *lam_out, float *dJdF, void *stream);
+
+/* Kinetic energy J = sum_x rho |u|^2 / 2 of the state in f (a state buffer;
+ * NULL = the current state), u with the +F/2 shift; per-cell values in
+ * FP32, summed in FP64.  out: host, 1 double.  Synchronises `stream`.
+ * Errors: LBM_EINVAL, LBM_ESTATE, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE. */
+lbm_status lbm_kinetic_energy(lbm_ctx *ctx, const void *f, double *out, void *stream);
+
+/* Seed of the adjoint of J: lam_out = dJ/df of the state in f (NULL =
+ * current), lam_a = u.e_a - |u|^2/2, and, when dJdF is not NULL, the direct
+ * term dJdF += u/2.  Errors: LBM_EINVAL, LBM_ESTATE, LBM_EUNSUPPORTED (D3Q15),
+ * LBM_ECUDA. */
+lbm_status lbm_kinetic_energy_seed(lbm_ctx *ctx, const void *f, float *lam_out, float *dJdF,
+                                   void *stream);
 
 /* Human-readable name of a status code (static string). */
 const char *lbm_status_string(lbm_status status);

@@ -1,0 +1,181 @@
+// Kernels of the discrete adjoint of the D3Q27 step and of the kinetic-energy
+// objective (not in the paper: the reverse mode of its update).
+//
+// Forward step (pull form): f_{t+1}[a](x) = C_a(f_t(x - e_a)), or, behind a
+// bounce-back wall, C_opp(a)(f_t(x)).  Its transpose for the adjoint
+// lam = dJ/df:
+//     lam_t(y) = J_C(f_t(y))^T mu(y),   mu_b(y) = lam_{t+1}[b](y + e_b)
+// (or lam_{t+1}[opp b](y) when y + e_b is behind a wall), and
+//     dJ/dF(y) += (dC/dF)^T mu(y).
+// Adjoint fields are FP32, laid out like the state (population planes of
+// pitched rows).
+#pragma once
+
+#include "adjoint_q27.cuh"
+#include "kernels.cuh"
+
+namespace lbm {
+
+struct AdjointArgs {
+    const float *lam_next[27];  // planes of lam_{t+1}
+    float *lam_out[27];         // planes of lam_t
+    float *gF;                  // dense [3][N] accumulator or nullptr
+};
+
+template <typename T, bool kWalls>
+__global__ void __launch_bounds__(128) adjoint_kernel(const StepIO<T> io, const AdjointArgs g,
+                                                      const StepArgs a) {
+    int x, y, z;
+    if (!cell_coords(a.g, x, y, z)) return;
+    const Rows<kWalls> R = pull_rows<kWalls>(a.g, y, z);
+    const int xs[3] = {(x + 1 == a.g.nx) ? 0 : x + 1, x, (x == 0) ? a.g.nx - 1 : x - 1};
+    float f[27], mu[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        const int i = ex<27>(q) + 1, j = ey<27>(q) + 1, k = ez<27>(q) + 1;
+        // state at t: pull from x - e_q
+        float v;
+        if (kWalls && R.wall[j][k])
+            v = Storage<T>::load(io.in[opposite<27>(q)] + R.own + x);
+        else
+            v = Storage<T>::load(io.in[q] + R.off[j][k] + xs[i]);
+        f[q] = Storage<T>::kScaled ? v * float(weight<27>(q)) : v;
+        // adjoint at t+1: from x + e_q (the mirrored pull)
+        if (kWalls && R.wall[2 - j][2 - k])
+            mu[q] = __ldg(g.lam_next[opposite<27>(q)] + R.own + x);
+        else
+            mu[q] = __ldg(g.lam_next[q] + R.off[2 - j][2 - k] + xs[2 - i]);
+    }
+    const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
+    const long long c = dense_index(a.g, x, y, z);
+    float Fx, Fy, Fz;
+    cell_force(a, c, N, Fx, Fy, Fz);
+    const Rates27<float> r = load_rates27(a);
+    float lam[27], gx, gy, gz;
+    adjoint27(f, Fx, Fy, Fz, r, mu, lam, gx, gy, gz);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) __stcs(g.lam_out[q] + R.own + x, lam[q]);
+    if (g.gF) {
+        g.gF[c] += gx;
+        g.gF[N + c] += gy;
+        g.gF[2 * N + c] += gz;
+    }
+}
+
+// Seed of the adjoint for J = sum_x rho |u|^2 / 2 at the final state:
+// lam_a = u.e_a - |u|^2 / 2, and the direct term dJ/dF += u / 2
+// (u = (j + F/2) / rho).
+template <typename T>
+__global__ void __launch_bounds__(128) energy_seed_kernel(const T *__restrict__ buf,
+                                                          const StepArgs a, AdjointArgs g) {
+    int x, y, z;
+    if (!cell_coords(a.g, x, y, z)) return;
+    float f[27];
+    gather<27, T>(buf, a.g, pull_sources(a.g, x, y, z), f);
+    float drho, jx, jy, jz, Fx, Fy, Fz;
+    moments<27>(f, drho, jx, jy, jz);
+    const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
+    const long long c = dense_index(a.g, x, y, z);
+    cell_force(a, c, N, Fx, Fy, Fz);
+    const float ir = 1.0f / (1.0f + drho);
+    const float ux = (jx + 0.5f * Fx) * ir, uy = (jy + 0.5f * Fy) * ir, uz = (jz + 0.5f * Fz) * ir;
+    const float h = 0.5f * (ux * ux + uy * uy + uz * uz);
+    const long long own = ((long long)z * a.g.ny + y) * a.g.px + x;
+#pragma unroll
+    for (int q = 0; q < 27; ++q)
+        g.lam_out[q][own] = ex<27>(q) * ux + ey<27>(q) * uy + ez<27>(q) * uz - h;
+    if (g.gF) {
+        g.gF[c] += 0.5f * ux;
+        g.gF[N + c] += 0.5f * uy;
+        g.gF[2 * N + c] += 0.5f * uz;
+    }
+}
+
+// Per-block partial sums of rho |u|^2 / 2 (slot 0 of each 4-double record),
+// rows assigned to blocks as in the conservation reduction.
+template <int Q, typename T>
+__global__ void __launch_bounds__(kRedThreads) energy_kernel(const T *__restrict__ buf,
+                                                             const StepArgs a,
+                                                             double *__restrict__ part) {
+    const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
+    const long long rows = (long long)a.g.ny * a.g.nz;
+    double acc = 0.0;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int y = int(row % a.g.ny), z = int(row / a.g.ny);
+        for (int x = threadIdx.x; x < a.g.nx; x += blockDim.x) {
+            float f[Q];
+            gather<Q, T>(buf, a.g, pull_sources(a.g, x, y, z), f);
+            float drho, jx, jy, jz, Fx, Fy, Fz;
+            moments<Q>(f, drho, jx, jy, jz);
+            cell_force(a, row * a.g.nx + x, N, Fx, Fy, Fz);
+            const float px = jx + 0.5f * Fx, py = jy + 0.5f * Fy, pz = jz + 0.5f * Fz;
+            acc += double(0.5f * (px * px + py * py + pz * pz) / (1.0f + drho));
+        }
+    }
+    __shared__ double sh[kRedThreads];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[4 * blockIdx.x] = sh[0];
+        part[4 * blockIdx.x + 1] = 0.0;
+        part[4 * blockIdx.x + 2] = 0.0;
+        part[4 * blockIdx.x + 3] = 0.0;
+    }
+}
+
+template <typename T>
+cudaError_t launch_adjoint(const void *f_t, const float *lam_next, float *lam_out, float *gF,
+                           const StepArgs &a, cudaStream_t st) {
+    StepIO<T> io;
+    AdjointArgs g;
+    for (int q = 0; q < 27; ++q) {
+        io.in[q] = static_cast<const T *>(f_t) + q * a.g.pop;
+        io.out[q] = nullptr;
+        g.lam_next[q] = lam_next + q * a.g.pop;
+        g.lam_out[q] = lam_out + q * a.g.pop;
+    }
+    g.gF = gF;
+    const CellLaunch L = cell_launch(a.g);
+    if (a.g.bc)
+        adjoint_kernel<T, true><<<L.grid, L.block, 0, st>>>(io, g, a);
+    else
+        adjoint_kernel<T, false><<<L.grid, L.block, 0, st>>>(io, g, a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_energy_seed(const void *f, float *lam_out, float *gF, const StepArgs &a,
+                               cudaStream_t st) {
+    AdjointArgs g;
+    for (int q = 0; q < 27; ++q) {
+        g.lam_next[q] = nullptr;
+        g.lam_out[q] = lam_out + q * a.g.pop;
+    }
+    g.gF = gF;
+    const CellLaunch L = cell_launch(a.g);
+    energy_seed_kernel<T><<<L.grid, L.block, 0, st>>>(static_cast<const T *>(f), a, g);
+    return cudaGetLastError();
+}
+
+template <int Q, typename T>
+cudaError_t launch_energy(const void *f, const StepArgs &a, double *part, int blocks,
+                          cudaStream_t st) {
+    energy_kernel<Q, T><<<blocks, kRedThreads, 0, st>>>(static_cast<const T *>(f), a, part);
+    return cudaGetLastError();
+}
+
+#define LBM_INSTANTIATE_ADJOINT(EXT, T)                                                          \
+    EXT template cudaError_t launch_adjoint<T>(const void *, const float *, float *, float *,   \
+                                               const StepArgs &, cudaStream_t);                 \
+    EXT template cudaError_t launch_energy_seed<T>(const void *, float *, float *,               \
+                                                   const StepArgs &, cudaStream_t);             \
+    EXT template cudaError_t launch_energy<27, T>(const void *, const StepArgs &, double *, int, \
+                                                  cudaStream_t);                                \
+    EXT template cudaError_t launch_energy<15, T>(const void *, const StepArgs &, double *, int, \
+                                                  cudaStream_t);
+
+}  // namespace lbm

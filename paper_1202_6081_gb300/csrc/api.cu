@@ -5,11 +5,14 @@
 #include <new>
 
 #include "../../include/lbm.h"
-#include "kernels.cuh"
+#include "adjoint_kernels.cuh"
 
 namespace lbm {
 LBM_INSTANTIATE(extern, 27)
 LBM_INSTANTIATE(extern, 15)
+LBM_INSTANTIATE_ADJOINT(extern, float)
+LBM_INSTANTIATE_ADJOINT(extern, __half)
+LBM_INSTANTIATE_ADJOINT(extern, __nv_bfloat16)
 }  // namespace lbm
 
 struct lbm_ctx {
@@ -67,6 +70,39 @@ cudaError_t dispatch(const lbm_ctx *c, Args &&...args) {
         default: return cudaErrorInvalidValue;
     }
 }
+
+// Dispatch on the storage type only (D3Q27 adjoint kernels).
+template <template <typename> class Fn, typename... Args>
+cudaError_t dispatch_storage(const lbm_ctx *c, Args &&...args) {
+    switch (int(c->storage)) {
+        case LBM_STORE_F32: return Fn<float>::run(args...);
+        case LBM_STORE_F16: return Fn<__half>::run(args...);
+        case LBM_STORE_BF16: return Fn<__nv_bfloat16>::run(args...);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+struct AdjointFn {
+    static cudaError_t run(const void *f, const float *ln, float *lo, float *gF,
+                           const lbm::StepArgs &a, cudaStream_t s) {
+        return lbm::launch_adjoint<T>(f, ln, lo, gF, a, s);
+    }
+};
+template <typename T>
+struct SeedFn {
+    static cudaError_t run(const void *f, float *lo, float *gF, const lbm::StepArgs &a,
+                           cudaStream_t s) {
+        return lbm::launch_energy_seed<T>(f, lo, gF, a, s);
+    }
+};
+template <int Q, typename T>
+struct EnergyFn {
+    static cudaError_t run(const void *f, const lbm::StepArgs &a, double *part, int blocks,
+                           cudaStream_t s) {
+        return lbm::launch_energy<Q, T>(f, a, part, blocks, s);
+    }
+};
 
 template <int Q, typename T>
 struct StepFn {
@@ -193,6 +229,13 @@ lbm_status lbm_set_force(lbm_ctx *c, const double *force) {
     return LBM_OK;
 }
 
+lbm_status lbm_set_force_field(lbm_ctx *c, const float *force_field) {
+    if (!c) return LBM_EINVAL;
+    if (force_field && (reinterpret_cast<uintptr_t>(force_field) & 3u)) return LBM_EINVAL;
+    c->Ffield = force_field;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_omega(lbm_ctx *c, const double *omega) {
     if (!c || !valid_rates(c->Q, omega)) return LBM_EINVAL;
     for (int b = 4; b < c->Q; ++b) c->w[b] = float(omega[b]);
@@ -251,14 +294,11 @@ lbm_status lbm_macroscopic(const lbm_ctx *c, float *rho, float *u, void *stream)
     return LBM_OK;
 }
 
-lbm_status lbm_conservation(lbm_ctx *c, double out[4], void *stream) {
-    if (!c || !out) return LBM_EINVAL;
-    if (!c->bound || !c->state_set) return LBM_ESTATE;
-    const long long N = (long long)c->g.nx * c->g.ny * c->g.nz;
-    const int blocks = lbm::conservation_blocks(c->g);
+static lbm_status ensure_scratch(lbm_ctx *c, int blocks) {
     if (!c->red_scratch || c->red_blocks < blocks) {
         if (c->red_scratch) cudaFree(c->red_scratch);
         c->red_scratch = nullptr;
+        c->red_blocks = 0;
         if (cudaMalloc(&c->red_scratch, sizeof(double) * (4 * size_t(blocks) + 4)) !=
             cudaSuccess) {
             cudaGetLastError();
@@ -266,6 +306,16 @@ lbm_status lbm_conservation(lbm_ctx *c, double out[4], void *stream) {
         }
         c->red_blocks = blocks;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_conservation(lbm_ctx *c, double out[4], void *stream) {
+    if (!c || !out) return LBM_EINVAL;
+    if (!c->bound || !c->state_set) return LBM_ESTATE;
+    const long long N = (long long)c->g.nx * c->g.ny * c->g.nz;
+    const int blocks = lbm::conservation_blocks(c->g);
+    const lbm_status ms = ensure_scratch(c, blocks);
+    if (ms != LBM_OK) return ms;
     const lbm::StepArgs a = step_args(c);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = dispatch<ConsFn>(c, (const void *)c->buf[c->cur], a, c->red_scratch, blocks, s);
@@ -284,6 +334,87 @@ lbm_status lbm_conservation(lbm_ctx *c, double out[4], void *stream) {
     for (int k = 0; k < 4; ++k)
         if (!std::isfinite(out[k])) return LBM_ENONFINITE;
     return LBM_OK;
+}
+
+size_t lbm_adjoint_bytes(const lbm_ctx *c) {
+    if (!c) return 0;
+    return size_t(c->Q) * size_t(c->g.pop) * sizeof(float);
+}
+
+const void *lbm_current_state(const lbm_ctx *c) {
+    if (!c || !c->bound || !c->state_set) return nullptr;
+    return c->buf[c->cur];
+}
+
+static bool state_buffer_ok(const void *p) {
+    return p && (reinterpret_cast<uintptr_t>(p) & 255u) == 0;
+}
+
+lbm_status lbm_step_into(lbm_ctx *c, const void *f_in, void *f_out, void *stream) {
+    if (!c || !state_buffer_ok(f_in) || !state_buffer_ok(f_out) || f_in == f_out)
+        return LBM_EINVAL;
+    const size_t bytes = lbm_state_bytes(c);
+    const char *a = static_cast<const char *>(f_in), *b = static_cast<const char *>(f_out);
+    if (a < b + bytes && b < a + bytes) return LBM_EINVAL;
+    const lbm::StepArgs args = step_args(c);
+    cudaError_t e = dispatch<StepFn>(c, f_in, f_out, args, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_step(lbm_ctx *c, const void *f_t, const float *lam_next, float *lam_out,
+                            float *dJdF, void *stream) {
+    if (!c || !state_buffer_ok(f_t) || !lam_next || !lam_out || lam_next == lam_out)
+        return LBM_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(lam_next) | reinterpret_cast<uintptr_t>(lam_out)) & 15u)
+        return LBM_EINVAL;
+    if (dJdF && (reinterpret_cast<uintptr_t>(dJdF) & 3u)) return LBM_EINVAL;
+    if (c->Q != 27) return LBM_EUNSUPPORTED;
+    const lbm::StepArgs a = step_args(c);
+    cudaError_t e = dispatch_storage<AdjointFn>(c, f_t, lam_next, lam_out, dJdF, a,
+                                                (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return LBM_OK;
+}
+
+lbm_status lbm_kinetic_energy_seed(lbm_ctx *c, const void *f, float *lam_out, float *dJdF,
+                                   void *stream) {
+    if (!c || !lam_out) return LBM_EINVAL;
+    if (!f) {
+        if (!c->bound || !c->state_set) return LBM_ESTATE;
+        f = c->buf[c->cur];
+    }
+    if (!state_buffer_ok(f) || (reinterpret_cast<uintptr_t>(lam_out) & 15u)) return LBM_EINVAL;
+    if (c->Q != 27) return LBM_EUNSUPPORTED;
+    const lbm::StepArgs a = step_args(c);
+    cudaError_t e = dispatch_storage<SeedFn>(c, f, lam_out, dJdF, a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return LBM_OK;
+}
+
+lbm_status lbm_kinetic_energy(lbm_ctx *c, const void *f, double *out, void *stream) {
+    if (!c || !out) return LBM_EINVAL;
+    if (!f) {
+        if (!c->bound || !c->state_set) return LBM_ESTATE;
+        f = c->buf[c->cur];
+    }
+    if (!state_buffer_ok(f)) return LBM_EINVAL;
+    const int blocks = lbm::conservation_blocks(c->g);
+    const lbm_status ms = ensure_scratch(c, blocks);
+    if (ms != LBM_OK) return ms;
+    const lbm::StepArgs a = step_args(c);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = dispatch<EnergyFn>(c, f, a, c->red_scratch, blocks, s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    double *tot = c->red_scratch + 4 * size_t(c->red_blocks);
+    e = lbm::launch_reduce_final(c->red_scratch, blocks, tot, s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    double h[4];
+    e = cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    *out = h[0];
+    return std::isfinite(h[0]) ? LBM_OK : LBM_ENONFINITE;
 }
 
 const char *lbm_status_string(lbm_status s) {

@@ -1,6 +1,8 @@
-// Explicit instantiation of the D3Q27 kernels with F32 storage.
-#include "kernels.cuh"
+// Explicit instantiation of the D3Q27 kernels (step, state, reductions,
+// adjoint) with F32 storage.
+#include "adjoint_kernels.cuh"
 
 namespace lbm {
 LBM_INSTANTIATE_1(, 27, float)
+LBM_INSTANTIATE_ADJOINT(, float)
 }  // namespace lbm

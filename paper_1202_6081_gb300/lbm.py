@@ -74,6 +74,13 @@ def load():
             "lbm_conservation": ([vp, dp, vp], ip),
             "lbm_status_string": ([ip], ctypes.c_char_p),
             "lbm_last_cuda_error": ([vp], ctypes.c_char_p),
+            "lbm_set_force_field": ([vp, vp], ip),
+            "lbm_adjoint_bytes": ([vp], ctypes.c_size_t),
+            "lbm_current_state": ([vp], vp),
+            "lbm_step_into": ([vp, vp, vp, vp], ip),
+            "lbm_adjoint_step": ([vp, vp, vp, vp, vp, vp], ip),
+            "lbm_kinetic_energy": ([vp, vp, dp, vp], ip),
+            "lbm_kinetic_energy_seed": ([vp, vp, vp, vp, vp], ip),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -88,9 +95,11 @@ def exported_symbols():
     lib = load()
     names = []
     for n in ("lbm_create", "lbm_destroy", "lbm_state_bytes", "lbm_row_pitch", "lbm_bind",
-              "lbm_set_force", "lbm_set_omega", "lbm_init_equilibrium", "lbm_set_state",
-              "lbm_get_state", "lbm_step", "lbm_macroscopic", "lbm_conservation",
-              "lbm_status_string", "lbm_last_cuda_error"):
+              "lbm_set_force", "lbm_set_force_field", "lbm_set_omega", "lbm_init_equilibrium",
+              "lbm_set_state", "lbm_get_state", "lbm_step", "lbm_macroscopic",
+              "lbm_conservation", "lbm_status_string", "lbm_last_cuda_error",
+              "lbm_adjoint_bytes", "lbm_current_state", "lbm_step_into", "lbm_adjoint_step",
+              "lbm_kinetic_energy", "lbm_kinetic_energy_seed"):
         getattr(lib, n)
         names.append(n)
     return names
@@ -190,6 +199,40 @@ def lbm_status_string(status):
     return load().lbm_status_string(int(status)).decode()
 
 
+def lbm_set_force_field(ctx, force_field):
+    _check(load().lbm_set_force_field(ctx, _ptr(force_field)), "lbm_set_force_field", ctx)
+
+
+def lbm_adjoint_bytes(ctx):
+    return int(load().lbm_adjoint_bytes(ctx))
+
+
+def lbm_current_state(ctx):
+    return load().lbm_current_state(ctx)
+
+
+def lbm_step_into(ctx, f_in, f_out, stream=None):
+    _check(load().lbm_step_into(ctx, _ptr(f_in), _ptr(f_out), _stream(stream)), "lbm_step_into",
+           ctx)
+
+
+def lbm_adjoint_step(ctx, f_t, lam_next, lam_out, dJdF=None, stream=None):
+    _check(load().lbm_adjoint_step(ctx, _ptr(f_t), _ptr(lam_next), _ptr(lam_out), _ptr(dJdF),
+                                   _stream(stream)), "lbm_adjoint_step", ctx)
+
+
+def lbm_kinetic_energy(ctx, f=None, stream=None):
+    out = ctypes.c_double()
+    _check(load().lbm_kinetic_energy(ctx, _ptr(f), ctypes.byref(out), _stream(stream)),
+           "lbm_kinetic_energy", ctx)
+    return float(out.value)
+
+
+def lbm_kinetic_energy_seed(ctx, f, lam_out, dJdF=None, stream=None):
+    _check(load().lbm_kinetic_energy_seed(ctx, _ptr(f), _ptr(lam_out), _ptr(dJdF),
+                                          _stream(stream)), "lbm_kinetic_energy_seed", ctx)
+
+
 # ---- convenience owner ----------------------------------------------------
 
 class Solver:
@@ -279,3 +322,51 @@ class Solver:
     def set_omega(self, omega):
         self.omega = np.asarray(omega, dtype=np.float64)
         lbm_set_omega(self.ctx, self.omega, self.Q)
+
+    def set_force_field(self, field):
+        """Bind a device FP32 force field [3, nz, ny, nx] (None: uniform)."""
+        if field is not None:
+            nz, ny, nx = self.shape
+            assert field.dtype == torch.float32 and field.is_contiguous()
+            assert tuple(field.shape) == (3, nz, ny, nx) and field.device == self.device
+        self.force_field = field
+        lbm_set_force_field(self.ctx, field)
+
+    # ---- state buffers (checkpoints) and the adjoint --------------------
+
+    def new_state_buffer(self):
+        return torch.empty(lbm_state_bytes(self.ctx), dtype=torch.uint8, device=self.device)
+
+    def current_buffer(self):
+        """The bound buffer tensor holding the current state."""
+        p = lbm_current_state(self.ctx)
+        for b in self.buffers:
+            if b.data_ptr() == p:
+                return b
+        raise RuntimeError("no current state")
+
+    def load_buffer(self, src):
+        """Make the state in buffer `src` the current state."""
+        self.current_buffer().copy_(src)
+
+    def step_into(self, src, dst, stream=None):
+        lbm_step_into(self.ctx, src, dst, stream)
+
+    def new_adjoint_field(self):
+        n = lbm_adjoint_bytes(self.ctx) // 4
+        return torch.zeros(n, dtype=torch.float32, device=self.device)
+
+    def adjoint_step(self, f_t, lam_next, lam_out, dJdF=None, stream=None):
+        lbm_adjoint_step(self.ctx, f_t, lam_next, lam_out, dJdF, stream)
+
+    def kinetic_energy(self, buf=None, stream=None):
+        return lbm_kinetic_energy(self.ctx, buf, stream)
+
+    def kinetic_energy_seed(self, buf, lam_out, dJdF=None, stream=None):
+        lbm_kinetic_energy_seed(self.ctx, buf, lam_out, dJdF, stream)
+
+    def adjoint_view(self, lam):
+        """Dense [Q, nz, ny, nx] view of a pitched adjoint field."""
+        nz, ny, nx = self.shape
+        px = lbm_row_pitch(self.ctx)
+        return lam.view(self.Q, nz, ny, px)[..., :nx]

@@ -1,0 +1,174 @@
+"""The discrete adjoint on the GPU (through the C ABI) against the FP64
+oracle's adjoint (complex-step Jacobians), against FP64 central finite
+differences of the oracle, and, at the 128^3 workload, against central
+finite differences of the GPU forward.
+
+J(F) = sum_x rho |u|^2 / 2 after n steps from a fixed initial state, as a
+function of the per-cell force field F used by the steps."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1202_6081_gb300 import build
+    from paper_1202_6081_gb300 import lbm as mod
+    build()
+    mod.load()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def to_pitched(S, dense):
+    lam = S.new_adjoint_field()
+    S.adjoint_view(lam).copy_(torch.as_tensor(dense, dtype=torch.float32))
+    return lam
+
+
+@pytest.mark.parametrize("bc", [0, 3])
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_adjoint_step_matches_oracle(lbm, orc, bc, storage):
+    Q = 27
+    shape = (6, 7, 10)
+    rho, u = W.taylor_green(shape, u0=0.05, noise=1e-2, seed=31)
+    om = W.random_omegas(Q, seed=32)
+    F = f32(W.rng(33).uniform(-1e-3, 1e-3, (3,) + shape))
+    lam_next = W.rng(34).standard_normal((Q,) + shape)
+    S = lbm.Solver(Q, shape, om, force=F, walls=bc, storage=storage)
+    S.init_equilibrium(rho, u)
+    f_t = S.current_buffer()
+    f_stored = S.get_state().cpu().numpy()
+    ln = to_pitched(S, lam_next)
+    lo = S.new_adjoint_field()
+    gF = torch.zeros((3,) + shape, dtype=torch.float32, device="cuda")
+    S.adjoint_step(f_t, ln, lo, gF)
+    torch.cuda.synchronize()
+    got = S.adjoint_view(lo).cpu().numpy()
+    gF_want = np.zeros((3,) + shape)
+    want = orc.adjoint_step(Q, shape, f_stored, F, om, lam_next, bc=bc, gF=gF_want)
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
+    assert np.abs(gF.cpu().numpy() - gF_want).max() <= 1e-5 * np.abs(gF_want).max()
+
+
+def test_kinetic_energy_and_seed_match_oracle(lbm, orc):
+    Q = 27
+    shape = (5, 8, 12)
+    rho, u = W.taylor_green(shape, u0=0.05, noise=1e-2, seed=35)
+    F = f32(W.rng(36).uniform(-1e-3, 1e-3, (3,) + shape))
+    S = lbm.Solver(Q, shape, W.omegas(Q, 1.4), force=F, walls=1)
+    S.init_equilibrium(rho, u)
+    f = S.get_state().cpu().numpy()
+    J = S.kinetic_energy()
+    assert J == pytest.approx(orc.kinetic_energy(Q, f, F), rel=1e-6)
+    lam = S.new_adjoint_field()
+    gF = torch.zeros((3,) + shape, dtype=torch.float32, device="cuda")
+    S.kinetic_energy_seed(S.current_buffer(), lam, gF)
+    dfl, dF = orc.kinetic_energy_grad(Q, f, F)
+    np.testing.assert_allclose(S.adjoint_view(lam).cpu().numpy(), dfl, atol=1e-7)
+    np.testing.assert_allclose(gF.cpu().numpy(), dF, atol=1e-8)
+
+
+def _cells(shape, k, seed):
+    cells = W.sample_cells(shape, k, seed=seed)
+    comps = W.rng(seed + 1).integers(0, 3, size=len(cells))
+    return [(int(c), tuple(int(v) for v in np.unravel_index(c, shape))) for c in cells], comps
+
+
+def test_gradient_matches_fp64_finite_differences(lbm, orc):
+    """16^3 periodic, Taylor-Green + noise, Gaussian force field (RMS 1e-5),
+    200 steps, checkpoint every 20: the GPU adjoint gradient matches FP64
+    central differences of the oracle (eps = 1e-6) on 16 sampled
+    (cell, component) pairs to 1e-3."""
+    from paper_1202_6081_gb300.autograd import kinetic_energy_after
+    Q = 27
+    shape = (16, 16, 16)
+    om = W.omegas(Q, 1 / 0.6)
+    rho, u = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    F0 = f32(W.gaussian_force_field(shape, rms=1e-5, sigma=4.0))
+    S = lbm.Solver(Q, shape, om)
+    Ft = torch.as_tensor(F0, dtype=torch.float32, device="cuda").contiguous().requires_grad_()
+    S.set_force_field(Ft.detach())
+    S.init_equilibrium(rho, u)
+    f0 = orc.equilibrium(Q, rho, u, F0)  # fixed initial state of the FD runs
+    J = kinetic_energy_after(S, Ft, 200, 20)
+    J.backward()
+    g = Ft.grad.cpu().numpy()
+    samples, comps = _cells(shape, 16, seed=41)
+    eps = 1e-6
+    fd = []
+    for (c, (z, y, x)), k in zip(samples, comps):
+        Fp = F0.copy()
+        Fp[k, z, y, x] += eps
+        Fm = F0.copy()
+        Fm[k, z, y, x] -= eps
+        jp = orc.kinetic_energy(Q, orc.run(Q, shape, f0, Fp, om, 200), Fp)
+        jm = orc.kinetic_energy(Q, orc.run(Q, shape, f0, Fm, om, 200), Fm)
+        fd.append((jp - jm) / (2 * eps))
+    fd = np.array(fd)
+    got = np.array([g[k, z, y, x] for (c, (z, y, x)), k in zip(samples, comps)])
+    print("fd", fd[:4], "adjoint", got[:4])
+    assert np.abs(got - fd).max() <= 1e-3 * np.abs(fd).max()
+
+
+def test_gradient_128cubed_matches_gpu_finite_differences(lbm):
+    """The adjoint workload: D3Q27, 128^3 periodic, tau = 0.6, Taylor-Green +
+    noise, Gaussian force field RMS 1e-5, J after 200 steps, checkpoint every
+    20: the gradient matches central differences of the GPU forward on 16
+    random cells to 1e-3 (relative to the largest sampled gradient)."""
+    from paper_1202_6081_gb300.autograd import kinetic_energy_after
+    Q = 27
+    shape = (128, 128, 128)
+    om = W.omegas(Q, 1 / 0.6)
+    rho, u = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    F0 = W.gaussian_force_field(shape, rms=1e-5, sigma=4.0).astype(np.float32)
+    S = lbm.Solver(Q, shape, om)
+    Ft = torch.as_tensor(F0, device="cuda").contiguous().requires_grad_()
+    S.set_force_field(Ft.detach())
+    S.init_equilibrium(rho, u)
+    init = S.current_buffer().clone()
+    J = kinetic_energy_after(S, Ft, 200, 20)
+    J.backward()
+    g = Ft.grad
+
+    def J_of(Fdev):
+        S.set_force_field(Fdev)
+        S.load_buffer(init)
+        S.step(200)
+        return S.kinetic_energy()
+
+    samples, comps = _cells(shape, 16, seed=42)
+    eps = 4e-5
+    fd, got = [], []
+    Fp = Ft.detach().clone()
+    for (c, (z, y, x)), k in zip(samples, comps):
+        base = float(Fp[k, z, y, x])
+        Fp[k, z, y, x] = base + eps
+        hi = float(Fp[k, z, y, x])
+        jp = J_of(Fp)
+        Fp[k, z, y, x] = base - eps
+        lo = float(Fp[k, z, y, x])
+        jm = J_of(Fp)
+        Fp[k, z, y, x] = base
+        fd.append((jp - jm) / (hi - lo))
+        got.append(float(g[k, z, y, x]))
+    fd, got = np.array(fd), np.array(got)
+    print("fd", fd[:4], "adjoint", got[:4])
+    assert np.abs(got - fd).max() <= 1e-3 * np.abs(fd).max()
