@@ -204,6 +204,25 @@ lbm_status lbm_kinetic_energy(lbm_ctx *ctx, const void *f, double *out, void *st
 lbm_status lbm_kinetic_energy_seed(lbm_ctx *ctx, const void *f, float *lam_out, float *dJdF,
                                    void *stream);
 
+/* Conservation sums for callers that cannot let the library allocate device
+ * memory (the paper has no counterpart; this is a library service).  Same
+ * sums as lbm_conservation, but asynchronous, into a caller buffer, and with
+ * no cudaMalloc or cudaFree: the per-row partial sums live in a fixed array
+ * inside the library, 2 MiB per GPU, held by every GPU that loads the
+ * library until the process exits.
+ *   out  device, 4 doubles (8-byte aligned): sum_x (rho - 1), then
+ *        sum_x rho u_x, rho u_y, rho u_z.  Note: the first value is the mass
+ *        minus the cell count nx*ny*nz (the FP64 sum of the density
+ *        deviations, without the large constant).
+ * Limit: ny * nz <= 65536 (one partial record per (y, z) row); larger grids
+ * return LBM_EINVAL.  The context's device must be current (LBM_ESTATE
+ * otherwise).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * race.  Errors: LBM_EINVAL, LBM_ESTATE, LBM_ECUDA, LBM_EUNSUPPORTED (device
+ * index >= 64). */
+lbm_status lbm_conservation_noalloc(lbm_ctx *ctx, double *out, void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *lbm_status_string(lbm_status status);
 

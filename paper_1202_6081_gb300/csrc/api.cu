@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "../../include/lbm.h"
@@ -415,6 +416,73 @@ lbm_status lbm_kinetic_energy(lbm_ctx *c, const void *f, double *out, void *stre
     if (e != cudaSuccess) return cuda_fail(c, e);
     *out = h[0];
     return std::isfinite(h[0]) ? LBM_OK : LBM_ENONFINITE;
+}
+
+// ---- conservation sums without any allocation ------------------------------
+//
+// Some callers cannot let a library call cudaMalloc: codes whose device
+// memory is planned once at start-up and handed out from their own pool (an
+// allocation by a library would fall outside that plan and can fail once
+// the pool holds the device), and loops that cannot afford the device-wide
+// synchronisation cudaMalloc and cudaFree may imply.  lbm_conservation
+// allocates its reduction scratch on first use; lbm_conservation_noalloc
+// keeps the same partial sums in the file-scope array below, which every GPU
+// that loads this library holds until the process exits.
+//
+// The array has room for one partial record (4 doubles) per (y, z) row of
+// the grid, for at most kNoAllocMaxRows rows (2 MiB).  Each call launches one
+// block per row, each block overwrites its own record, and the final
+// reduction reads only the records this call wrote, so no part of the array
+// has to start at zero; it keeps the last call's contents.  Calls share the
+// array: two calls whose work overlaps on the GPU (different streams, or
+// different host threads) race on it.
+constexpr int kNoAllocMaxRows = 65536;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) double g_noalloc_part[4 * kNoAllocMaxRows];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kNoAllocMaxDevices];  // device address of the array, per device
+
+// Device address of g_noalloc_part on the current device.  In host code the
+// name g_noalloc_part is only a host-side stand-in for the device array, so
+// its address is looked up once per device, with that device current.
+lbm_status noalloc_scratch(int device, double **out) {
+    if (device < 0 || device >= kNoAllocMaxDevices) return LBM_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_part);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return LBM_ECUDA;
+        }
+        g_noalloc_ptr[device] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return LBM_OK;
+}
+}  // namespace
+
+lbm_status lbm_conservation_noalloc(lbm_ctx *c, double *out, void *stream) {
+    if (!c || !out || (reinterpret_cast<uintptr_t>(out) & 7u)) return LBM_EINVAL;
+    if (!c->bound || !c->state_set) return LBM_ESTATE;
+    const long long rows = (long long)c->g.ny * c->g.nz;
+    if (rows > kNoAllocMaxRows) return LBM_EINVAL;  // grid beyond the array's capacity
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
+    if (dev != c->device) return LBM_ESTATE;  // the context's device must be current
+    double *part = nullptr;
+    const lbm_status st = noalloc_scratch(dev, &part);
+    if (st != LBM_OK) return st;
+    const lbm::StepArgs a = step_args(c);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = dispatch<ConsFn>(c, (const void *)c->buf[c->cur], a, part, int(rows), s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    e = lbm::launch_reduce_final(part, int(rows), out, s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return LBM_OK;
 }
 
 const char *lbm_status_string(lbm_status s) {

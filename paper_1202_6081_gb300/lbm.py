@@ -81,6 +81,7 @@ def load():
             "lbm_adjoint_step": ([vp, vp, vp, vp, vp, vp], ip),
             "lbm_kinetic_energy": ([vp, vp, dp, vp], ip),
             "lbm_kinetic_energy_seed": ([vp, vp, vp, vp, vp], ip),
+            "lbm_conservation_noalloc": ([vp, vp, vp], ip),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -99,7 +100,7 @@ def exported_symbols():
               "lbm_set_state", "lbm_get_state", "lbm_step", "lbm_macroscopic",
               "lbm_conservation", "lbm_status_string", "lbm_last_cuda_error",
               "lbm_adjoint_bytes", "lbm_current_state", "lbm_step_into", "lbm_adjoint_step",
-              "lbm_kinetic_energy", "lbm_kinetic_energy_seed"):
+              "lbm_kinetic_energy", "lbm_kinetic_energy_seed", "lbm_conservation_noalloc"):
         getattr(lib, n)
         names.append(n)
     return names
@@ -226,6 +227,13 @@ def lbm_kinetic_energy(ctx, f=None, stream=None):
     _check(load().lbm_kinetic_energy(ctx, _ptr(f), ctypes.byref(out), _stream(stream)),
            "lbm_kinetic_energy", ctx)
     return float(out.value)
+
+
+def lbm_conservation_noalloc(ctx, out, stream=None):
+    """Asynchronous conservation sums into the device tensor `out` (4 FP64:
+    sum (rho - 1), sum rho u) without any allocation by the library."""
+    _check(load().lbm_conservation_noalloc(ctx, _ptr(out), _stream(stream)),
+           "lbm_conservation_noalloc", ctx)
 
 
 def lbm_kinetic_energy_seed(ctx, f, lam_out, dJdF=None, stream=None):
