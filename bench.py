@@ -34,7 +34,7 @@ UNIT = "MLUPS"
 BYTES_PER_CELL = {("q27", "f32"): 216, ("q27", "f16"): 108, ("q27", "bf16"): 108,
                   ("q15", "f32"): 120}
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["lattice.cuh", "vec2.cuh", "collide_q27.cuh", "kernels.cuh", "kernels_q27_f32.cu"]
+KERNEL_SOURCES = ["lattice.cuh", "vec2.cuh", "collide_q27.cuh", "kernels.cuh"]
 
 
 def parse():
