@@ -46,6 +46,12 @@ def parse():
     p.add_argument("--size", type=int, default=256, help="cube edge of the main workload")
     p.add_argument("--quick", action="store_true",
                    help="main measurement only (no e2e, sweeps, 16-bit or CPU baseline)")
+    p.add_argument("--lattice", type=int, choices=[27, 15], default=27,
+                   help="lattice of the main measurement (profiling runs)")
+    p.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
+                   help="storage of the main measurement (profiling runs)")
+    p.add_argument("--adjoint-only", action="store_true",
+                   help="time only the adjoint workload at --size (profiling runs)")
     return p.parse_args()
 
 
@@ -362,7 +368,13 @@ def run_ours(args):
     from paper_1202_6081_gb300 import build, lbm
     build()
     size = args.size
-    S, _, _ = make_solver(lbm, 27, size, "f32", 0.6)
+    if args.adjoint_only:
+        if rank == 0:
+            print(json.dumps({"adjoint": adjoint_timing(torch, lbm, size, steps=args.steps)}),
+                  flush=True)
+        return 0
+    lat, st = args.lattice, args.storage
+    S, _, _ = make_solver(lbm, lat, size, st, 0.6)
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -378,21 +390,23 @@ def run_ours(args):
     value = world * cells * args.steps / elapsed / 1e6
     peaks, peak_kind = measured_peaks()
     per_launch = elapsed / args.steps
-    alg_bytes = BYTES_PER_CELL[("q27", "f32")] * cells
+    bpc = BYTES_PER_CELL.get(("q%d" % lat, st), (4 if st == "f32" else 2) * 2 * lat)
+    alg_bytes = bpc * cells
     achieved = alg_bytes / per_launch / 1e9
     peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_launch * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "D3Q27 Taylor-Green+noise %d^3 periodic, tau=0.6, FP32 storage "
-                               "of f-w" % size,
+        "config": {"workload": "D3Q%d Taylor-Green+noise %d^3 periodic, tau=0.6, %s storage "
+                               "of f-w" % (lat, size, st.upper()),
                    "cells": cells, "l2": "no flush: inputs larger than L2 (2 x %.1f GB state)"
                    % (alg_bytes / 2 / 1e9), "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(size),
+                     "frac": achieved / peak,
+                     "traffic": ncu_traffic(size) if (lat, st) == (27, "f32") else None,
                      "peak_source": "%s hbm_gbs (copy), %d B/cell algorithmic" % (
-                         peak_kind, BYTES_PER_CELL[("q27", "f32")])},
+                         peak_kind, bpc)},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "conservation": {"mass": cons[0], "momentum": list(cons[1:])},

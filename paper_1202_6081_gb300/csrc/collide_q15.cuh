@@ -75,14 +75,19 @@ __device__ __forceinline__ void source15(float Fx, float Fy, float Fz, float ux,
     m[13] = Fx * uy * uz + Fy * ux * uz + Fz * ux * uy;
     m[14] = 20.0f * (fux * (3.0f * (uy2 + uz2) - 4.0f) + fuy * (3.0f * (ux2 + uz2) - 4.0f) +
                      fuz * (3.0f * (ux2 + uy2) - 4.0f));
-#pragma unroll
-    for (int a = 0; a < 15; ++a) {
+    static_for<15>([&](auto ia) {
+        constexpr int a = decltype(ia)::value;
         float s = 0.0f;
-#pragma unroll
-        for (int b = 1; b < 15; ++b)
-            if (k15(b, a) != 0) s = fmaf(float(k15(b, a)) / float(d15(b)), m[b], s);
+        static_for<15>([&](auto ib) {
+            constexpr int b = decltype(ib)::value;
+            constexpr int k = k15(b, a);
+            if constexpr (b >= 1 && k != 0) {
+                constexpr float c = float(k) / float(d15(b));
+                s = fmaf(c, m[b], s);
+            }
+        });
         S[a] = s;
-    }
+    });
 }
 
 // The cascade on deviation raw moments.  dk*: raw moments of the deviations
@@ -93,26 +98,36 @@ __device__ __forceinline__ void kernels15(const float (&f)[15], float Fx, float 
     float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
     float kxy = 0.f, kxz = 0.f, kyz = 0.f, kxx = 0.f, kyy = 0.f, kzz = 0.f;
     float kxyy = 0.f, kxxy = 0.f, kxxz = 0.f, kxyz = 0.f, kxxyy = 0.f;
-#pragma unroll
-    for (int a = 0; a < 15; ++a) {
-        const int x = q15_e(a, 0), y = q15_e(a, 1), z = q15_e(a, 2);
+    static_for<15>([&](auto ia) {
+        constexpr int a = decltype(ia)::value;
+        constexpr int x = q15_e(a, 0), y = q15_e(a, 1), z = q15_e(a, 2);
         const float v = f[a];
         drho += v;
-        if (x) jx += x * v;
-        if (y) jy += y * v;
-        if (z) jz += z * v;
-        if (x * y) kxy += (x * y) * v;
-        if (x * z) kxz += (x * z) * v;
-        if (y * z) kyz += (y * z) * v;
-        if (x) kxx += v;
-        if (y) kyy += v;
-        if (z) kzz += v;
-        if (x * y) kxyy += x * v;
-        if (x * y) kxxy += y * v;
-        if (x * z) kxxz += z * v;
-        if (x * y * z) kxyz += (x * y * z) * v;
-        if (x * y) kxxyy += v;
-    }
+        if constexpr (x != 0) {
+            jx += x * v;
+            kxx += v;
+        }
+        if constexpr (y != 0) {
+            jy += y * v;
+            kyy += v;
+        }
+        if constexpr (z != 0) {
+            jz += z * v;
+            kzz += v;
+        }
+        if constexpr (x * y != 0) {
+            kxy += (x * y) * v;
+            kxyy += x * v;
+            kxxy += y * v;
+            kxxyy += v;
+        }
+        if constexpr (x * z != 0) {
+            kxz += (x * z) * v;
+            kxxz += z * v;
+        }
+        if constexpr (y * z != 0) kyz += (y * z) * v;
+        if constexpr (x * y * z != 0) kxyz += (x * y * z) * v;
+    });
     const float rho = 1.0f + drho;
     const float inv_rho = 1.0f / rho;
     ux = (jx + 0.5f * Fx) * inv_rho;
@@ -181,14 +196,16 @@ __device__ __forceinline__ void collide15(float (&f)[15], float Fx, float Fy, fl
     float g[15], S[15], ux, uy, uz;
     kernels15(f, Fx, Fy, Fz, r, ux, uy, uz, g);
     source15(Fx, Fy, Fz, ux, uy, uz, S);
-#pragma unroll
-    for (int a = 0; a < 15; ++a) {
+    static_for<15>([&](auto ia) {
+        constexpr int a = decltype(ia)::value;
         float s = f[a] + S[a];
-#pragma unroll
-        for (int b = 4; b < 15; ++b)
-            if (k15(b, a) != 0) s = fmaf(float(k15(b, a)), g[b], s);
+        static_for<15>([&](auto ib) {
+            constexpr int b = decltype(ib)::value;
+            constexpr int k = k15(b, a);
+            if constexpr (b >= 4 && k != 0) s = fmaf(float(k), g[b], s);
+        });
         f[a] = s;
-    }
+    });
 }
 
 // Deviations of f = f^at(rho, u) - S/2: one collision with every omega = 1
@@ -197,11 +214,12 @@ __device__ __forceinline__ void collide15(float (&f)[15], float Fx, float Fy, fl
 __device__ __forceinline__ void equilibrium15(float drho, float ux, float uy, float uz, float Fx,
                                               float Fy, float Fz, float (&f)[15]) {
     const float rho = 1.0f + drho;
-#pragma unroll
-    for (int a = 0; a < 15; ++a) {
-        const float eu = q15_e(a, 0) * ux + q15_e(a, 1) * uy + q15_e(a, 2) * uz;
+    static_for<15>([&](auto ia) {
+        constexpr int a = decltype(ia)::value;
+        constexpr int cx = q15_e(a, 0), cy = q15_e(a, 1), cz = q15_e(a, 2);
+        const float eu = cx * ux + cy * uy + cz * uz;
         f[a] = float(weight<15>(a)) * (drho + 3.0f * rho * eu);
-    }
+    });
     RelaxRates15 ones;
 #pragma unroll
     for (int b = 0; b < 15; ++b) ones.w[b] = 1.0f;
@@ -209,14 +227,16 @@ __device__ __forceinline__ void equilibrium15(float drho, float ux, float uy, fl
     kernels15(f, 0.0f, 0.0f, 0.0f, ones, ux0, uy0, uz0, g);
     float S[15];
     source15(Fx, Fy, Fz, ux, uy, uz, S);
-#pragma unroll
-    for (int a = 0; a < 15; ++a) {
+    static_for<15>([&](auto ia) {
+        constexpr int a = decltype(ia)::value;
         float s = f[a];
-#pragma unroll
-        for (int b = 4; b < 15; ++b)
-            if (k15(b, a) != 0) s = fmaf(float(k15(b, a)), g[b], s);
+        static_for<15>([&](auto ib) {
+            constexpr int b = decltype(ib)::value;
+            constexpr int k = k15(b, a);
+            if constexpr (b >= 4 && k != 0) s = fmaf(float(k), g[b], s);
+        });
         f[a] = s - 0.5f * S[a];
-    }
+    });
 }
 
 }  // namespace lbm

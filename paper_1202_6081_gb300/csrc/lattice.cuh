@@ -24,7 +24,22 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace lbm {
+
+// Compile-time loop: calls f(std::integral_constant<int, i>) for i = 0..N-1,
+// so table lookups on i fold to constants whatever the unroller decides
+// (read the index as decltype(arg)::value inside f).
+template <typename F, int... Is>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, Is...>) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 constexpr unsigned kWallY = 1u;
 constexpr unsigned kWallZ = 2u;
