@@ -1,0 +1,184 @@
+"""Validation problems of the paper's Sec. 9 on the GPU path: the plates
+sweep across the stated Reynolds numbers, the grid-convergence study under
+diffusive scaling, and Womersley flow under a time-periodic force (with
+oracle parity of the time-dependent forcing).
+
+Geometry: the paper's N nodes across the channel include the two wall
+nodes; with half-way bounce-back the N - 2 fluid cells sit between walls
+half a cell outside them, L = (N - 2) / 2 (this reproduces the stated Wo
+and, within about 1 %, the stated Re)."""
+import numpy as np
+import pytest
+
+import analytic
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1202_6081_gb300 import build
+    from paper_1202_6081_gb300 import lbm as mod
+    build()
+    mod.load()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def plates_steady(lbm, Q, N, omega_nu, Fx):
+    """Steady force-driven flow between plates: 3 x 3 x (N - 2) fluid cells,
+    walls on the z faces; returns (z, u_x(z), u_analytic(z), nu, L)."""
+    nz = N - 2
+    shape = (nz, 3, 3)
+    L = nz / 2
+    nu = analytic.viscosity(omega_nu)
+    S = lbm.Solver(Q, shape, W.omegas(Q, omega_nu), force=(Fx, 0.0, 0.0), walls=lbm.LBM_WALL_Z)
+    S.init_equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    # the slowest mode decays as exp(-nu (pi / 2L)^2 t): run to e^-16
+    steps = int(16 * 4 * L * L / (nu * np.pi**2)) + 1
+    S.step(steps)
+    _, u = S.macroscopic()
+    ux = u[0].double().mean(dim=(1, 2)).cpu().numpy()
+    z = np.arange(nz) + 0.5 - L
+    return z, ux, analytic.plates_profile(z, L, Fx, nu), nu, L
+
+
+@pytest.mark.parametrize("Q,omega_nu,Fx,Re", [
+    (15, 1.818, 2e-7, 3.6), (15, 1.818, 4e-7, 7.2), (15, 1.818, 6e-7, 10.7),
+    (27, 1.818, 2e-7, 3.6), (27, 1.818, 4e-7, 7.2), (27, 1.818, 6e-7, 10.7),
+    (15, 1.923, 1e-6, 111.8), (15, 1.961, 1e-6, 447.2)])
+def test_plates_sweep_reynolds_numbers(lbm, Q, omega_nu, Fx, Re):
+    """Sec. 9 plates, 3 x 3 x 45 nodes: the steady profile matches
+    u0 (1 - (z/L)^2); the centre-line Reynolds number u_max L / nu matches the
+    closed form F L^3 / (2 nu^2) and, within the paper's rounding and its
+    unstated conventions (about 1 %), the value it states (3.6, 7.2, 10.7 at
+    omega 1.818; 111.8, 447.2 at 1.923, 1.961)."""
+    z, ux, ua, nu, L = plates_steady(lbm, Q, 45, omega_nu, Fx)
+    err = np.linalg.norm(ux - ua) / np.linalg.norm(ua)
+    re = ux.max() * L / nu
+    re_exact = ua.max() * L / nu
+    print("D3Q%d omega %.3f F %.1e: Re %.2f (closed form %.2f, paper %.1f), rel L2 %.2e" % (
+        Q, omega_nu, Fx, re, re_exact, Re, err))
+    assert err <= 1e-2
+    assert re == pytest.approx(re_exact, rel=1e-2)
+    assert re == pytest.approx(Re, rel=2e-2)
+
+
+def _oracle_plates_error(orc, Q, N, omega_nu, Fx):
+    nz = N - 2
+    L = nz / 2
+    shape = (nz, 1, 1)
+    nu = analytic.viscosity(omega_nu)
+    F = np.array([np.float32(Fx), 0.0, 0.0])
+    f = orc.equilibrium(Q, np.ones(shape), np.zeros((3,) + shape), F)
+    steps = int(16 * 4 * L * L / (nu * np.pi**2)) + 1
+    f = orc.run(Q, shape, f, F, W.omegas(Q, omega_nu), steps, bc=orc.WALL_Z)
+    _, u = orc.macroscopic(Q, f, F)
+    z = np.arange(nz) + 0.5 - L
+    ua = analytic.plates_profile(z, L, Fx, nu)
+    return np.linalg.norm(u[0, :, 0, 0] - ua) / np.linalg.norm(ua)
+
+
+def test_grid_convergence_matches_fp64(lbm, orc):
+    """Sec. 9 convergence study (D3Q15, 3 x 3 x N, omega 1.818, F_x = 6.958e-6
+    at N = 13 scaled as 1/L^3, diffusive scaling).  At N = 13 and 25 the
+    FP32 GPU errors equal the FP64 oracle's (second order: the oracle's slope
+    against L is -2.0, pinned in test_oracle_pins).  Finer grids meet the
+    FP32 storage floor: the scaled force per step (9e-8 at N = 49, 1e-8 at
+    N = 97) is a few hundred ulps of the stored deviations and the same
+    rounding repeats every step at steady state, so the error stops falling
+    near 3e-4; those are printed, not held."""
+    L13 = (13 - 2) / 2
+    for N in (13, 25, 49, 97):
+        L = (N - 2) / 2
+        Fx = 6.958e-6 * (L13 / L) ** 3
+        z, ux, ua, nu, _ = plates_steady(lbm, 15, N, 1.818, Fx)
+        err = np.linalg.norm(ux - ua) / np.linalg.norm(ua)
+        if N <= 25:
+            want = _oracle_plates_error(orc, 15, N, 1.818, Fx)
+            print("N %d: F %.3e, rel L2 error %.4e (FP64 oracle %.4e)" % (N, Fx, err, want))
+            assert err == pytest.approx(want, rel=1e-2)
+        else:
+            print("N %d: F %.3e, rel L2 error %.4e" % (N, Fx, err))
+            assert err <= 1e-3
+
+
+def _womersley_run(lbm, Q, omega_nu, steps, T=10000, Fm=1e-5, sample_every=None, u0=None):
+    nz = 43
+    shape = (nz, 3, 3)
+    S = lbm.Solver(Q, shape, W.omegas(Q, omega_nu), walls=lbm.LBM_WALL_Z)
+    u = np.zeros((3,) + shape)
+    if u0 is not None:
+        u[0] = u0[:, None, None]
+    S.set_force((Fm, 0.0, 0.0))
+    S.init_equilibrium(np.ones(shape), u)
+    Om = 2 * np.pi / T
+    out = {}
+    for n in range(steps):
+        S.set_force((Fm * np.cos(Om * n), 0.0, 0.0))
+        S.step(1)
+        if sample_every and (n + 1) % sample_every == 0:
+            S.set_force((Fm * np.cos(Om * (n + 1)), 0.0, 0.0))
+            _, u = S.macroscopic()
+            out[n + 1] = u[0].double().mean(dim=(1, 2)).cpu().numpy()
+    return S, out
+
+
+def test_womersley_time_dependent_force_matches_oracle(lbm, orc):
+    """The force changes every step (F = F_m cos(Omega t)); the GPU state after
+    300 steps matches the FP64 oracle stepped with the same forces."""
+    for Q in (15, 27):
+        T, Fm, om_nu = 200, 1e-3, 1.724
+        S, _ = _womersley_run(lbm, Q, om_nu, 300, T=T, Fm=Fm)
+        torch.cuda.synchronize()
+        f_gpu = S.get_state().cpu().numpy()
+        shape = (43, 3, 3)
+        # the GPU run starts from f^at - S(F(0))/2 with F(0) = F_m
+        f = orc.equilibrium(Q, np.ones(shape), np.zeros((3,) + shape),
+                            np.array([np.float32(Fm), 0.0, 0.0]))
+        om = W.omegas(Q, om_nu)
+        Om = 2 * np.pi / T
+        for n in range(300):
+            Fn = np.array([np.float32(Fm * np.cos(Om * n)), 0.0, 0.0])
+            f = orc.run(Q, shape, f, Fn, om, 1, bc=orc.WALL_Z)
+        w = orc.equilibrium(Q, np.ones((1, 1, 1)), np.zeros((3, 1, 1, 1)), np.zeros(3))
+        err = np.linalg.norm(f_gpu - f) / np.linalg.norm(f - w)
+        assert err <= 1e-5, (Q, err)
+
+
+@pytest.mark.parametrize("omega_nu,Wo", [(1.724, 3.3), (1.923, 6.6)])
+def test_womersley_profiles_match_analytic(lbm, omega_nu, Wo):
+    """Sec. 9 Womersley flow (D3Q15, 3 x 3 x 45 nodes, F_m = 1e-5,
+    T = 10000), started from the analytic profile at t = 0: over the second
+    period the profiles at eight phases match Re[U(z) e^{i Omega t}]
+    (prefactor -i F_m / Omega), and the Womersley number L sqrt(Omega / nu)
+    is the stated one."""
+    T = 10000
+    L = 43 / 2
+    nu = analytic.viscosity(omega_nu)
+    Om = 2 * np.pi / T
+    assert L * np.sqrt(Om / nu) == pytest.approx(Wo, abs=0.05)
+    z = np.arange(43) + 0.5 - L
+    u_start = analytic.womersley_profile(z, L, 1e-5, Om, nu, 0)
+    _, prof = _womersley_run(lbm, 15, omega_nu, 2 * T, T=T, sample_every=T // 8, u0=u_start)
+    errs = []
+    scale = max(np.abs(analytic.womersley_profile(z, L, 1e-5, Om, nu, t)).max()
+                for t in range(T, 2 * T, T // 8))
+    for t, ux in sorted(prof.items()):
+        if t <= T:
+            continue
+        ua = analytic.womersley_profile(z, L, 1e-5, Om, nu, t)
+        errs.append(np.abs(ux - ua).max() / scale)
+    print("Wo %.1f: max error / max |u| over the period: %.2e" % (Wo, max(errs)))
+    assert max(errs) <= 1e-2

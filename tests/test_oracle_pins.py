@@ -391,3 +391,30 @@ def test_viscosity_relation():
     L = 21.5
     u0 = 2e-7 * L**2 / (2 * nu)
     assert u0 * L / nu == pytest.approx(3.6, abs=0.05)
+
+
+@pytest.mark.slow
+def test_grid_convergence_under_diffusive_scaling(oracle_lib):
+    """Sec. 9 convergence study: D3Q15 plates, omega 1.818, N = 13, 25, 49
+    nodes across (L = (N - 2) / 2), F_x = 6.958e-6 at N = 13 scaled as
+    1/L^3.  The relative L2 velocity error is second order: its log-log slope
+    against L is -2 (the paper reports -1.96)."""
+    Q = 15
+    errs, Ls = [], []
+    for N in (13, 25, 49):
+        nz = N - 2
+        L = nz / 2
+        shape = (nz, 1, 1)
+        nu = analytic.viscosity(1.818)
+        Fx = 6.958e-6 * (5.5 / L) ** 3
+        F = np.array([Fx, 0.0, 0.0])
+        f = oracle_lib.equilibrium(Q, np.ones(shape), np.zeros((3,) + shape), F)
+        steps = int(16 * 4 * L * L / (nu * np.pi**2)) + 1
+        f = oracle_lib.run(Q, shape, f, F, W.omegas(Q, 1.818), steps, bc=oracle_lib.WALL_Z)
+        _, u = oracle_lib.macroscopic(Q, f, F)
+        z = np.arange(nz) + 0.5 - L
+        ua = analytic.plates_profile(z, L, Fx, nu)
+        errs.append(np.linalg.norm(u[0, :, 0, 0] - ua) / np.linalg.norm(ua))
+        Ls.append(L)
+    slope = np.polyfit(np.log(Ls), np.log(errs), 1)[0]
+    assert -2.1 <= slope <= -1.9
