@@ -355,6 +355,21 @@ def adjoint_timing(torch, lbm, size, steps=100):
                                    "backward_forward_ratio": (t2 - t1) / (t1 - t0)}}
 
 
+def max_over_ranks(torch, value, device):
+    """The largest value over the ranks of the default process group (the
+    slowest rank's time).  Timing only: no simulation data is exchanged."""
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world, cells, steps, elapsed):
+    """Cell updates of all ranks (independent replicas of the same workload)
+    per second of the slowest rank, in millions."""
+    return world * cells * steps / elapsed / 1e6
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -382,12 +397,9 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     cons = S.conservation()
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(torch, elapsed, "cuda")
     cells = size**3
-    value = world * cells * args.steps / elapsed / 1e6
+    value = whole_job_mlups(world, cells, args.steps, elapsed)
     peaks, peak_kind = measured_peaks()
     per_launch = elapsed / args.steps
     bpc = BYTES_PER_CELL.get(("q%d" % lat, st), (4 if st == "f32" else 2) * 2 * lat)

@@ -269,3 +269,38 @@ def test_full_size_sampled_step_256(lbm, orc):
     N = 256**3
     assert abs(c1[0] - c0[0]) <= 1e-8 * N
     np.testing.assert_allclose(c1[1:], c0[1:], atol=1e-6 * N * 1e-3)
+
+
+def test_calls_out_of_order_and_non_finite_state_are_reported(lbm):
+    """Failure detection without any GPU fault: calls out of order return
+    LBM_ESTATE; a NaN planted in the host-side initial field is caught by the
+    FP64 conservation reduction as LBM_ENONFINITE (no trap, the context stays
+    usable)."""
+    import ctypes
+    lib = lbm.load()
+    shape = (4, 5, 6)
+    ctx = lbm.lbm_create(27, 6, 5, 4, W.omegas(27, 1.2))
+    try:
+        assert lib.lbm_step(ctx, 1, None) == 3               # not bound
+        a = torch.empty(lbm.lbm_state_bytes(ctx), dtype=torch.uint8, device="cuda")
+        b = torch.empty_like(a)
+        lbm.lbm_bind(ctx, a, b)
+        assert lib.lbm_step(ctx, 1, None) == 3               # bound, no state yet
+        out = (ctypes.c_double * 4)()
+        assert lib.lbm_conservation(ctx, out, None) == 3
+        assert lib.lbm_bind(ctx, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(a.data_ptr()),
+                            None) == 1                       # aliased buffers
+        rho = np.ones(shape)
+        rho[1, 2, 3] = np.nan
+        r = torch.as_tensor(rho, device="cuda")
+        u = torch.zeros((3,) + shape, dtype=torch.float64, device="cuda")
+        lbm.lbm_init_equilibrium(ctx, r, u)
+        assert lib.lbm_conservation(ctx, out, None) == 5     # LBM_ENONFINITE
+        assert not np.isfinite(out[0])
+        # the context and the GPU keep working: a clean state steps normally
+        lbm.lbm_init_equilibrium(ctx, torch.ones_like(r), u)
+        lbm.lbm_step(ctx, 3)
+        assert lbm.lbm_conservation(ctx)[0] == pytest.approx(np.prod(shape), rel=1e-12)
+    finally:
+        torch.cuda.synchronize()
+        lbm.lbm_destroy(ctx)
