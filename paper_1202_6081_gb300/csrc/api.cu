@@ -43,6 +43,7 @@ lbm::StepArgs step_args(const lbm_ctx *c) {
     for (int b = 0; b < 27; ++b) a.w[b] = c->w[b];
     for (int i = 0; i < 3; ++i) a.F[i] = c->F[i];
     a.Ffield = c->Ffield;
+    a.has_force = (c->Ffield || c->F[0] != 0.0f || c->F[1] != 0.0f || c->F[2] != 0.0f) ? 1 : 0;
     return a;
 }
 

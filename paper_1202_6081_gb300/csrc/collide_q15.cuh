@@ -8,6 +8,14 @@
 // higher ones), then f~ = f + K.g + S with K the D3Q15 basis and
 // S = K D^-1 m^s the source of App. G.
 //
+// GB300 form: templated on the value type (float, or f2 = two neighbouring
+// cells in packed f32x2 arithmetic), and the update K.g + S is evaluated by
+// sign patterns instead of a 15 x 11 product: on the 8 corners
+// (sx, sy, sz) every basis vector is one of 1, sx, sy, sz, sx sy, sx sz,
+// sy sz, sx sy sz times a constant, so the 8 increments are a three-level
+// butterfly of 8 coefficients; each axis pair (+-x etc.) is an even part plus
+// or minus an odd part.
+//
 // Precision: the state is carried as deviations from the weights
 // (2/9, 1/9, 1/72).  The weights' raw moments are 1 (mass), 1/3 (xx, yy, zz)
 // and 1/9 (xxyy), zero otherwise; wherever such a constant meets its
@@ -15,6 +23,7 @@
 #pragma once
 
 #include "lattice.cuh"
+#include "vec2.cuh"
 
 namespace lbm {
 
@@ -41,171 +50,241 @@ __host__ __device__ constexpr int k15(int b, int a) {
     }
 }
 
-// <K_beta|K_beta> on D3Q15
-__host__ __device__ constexpr int d15(int b) {
-    int s = 0;
-    for (int a = 0; a < 15; ++a) s += k15(b, a) * k15(b, a);
-    return s;
+// App. G prefactors 1/k_beta of the kernels g_4..g_14 (omega_beta / k_beta).
+__host__ __device__ constexpr float k15_inv(int b) {
+    return b <= 6 ? 0.125f
+         : b == 7 ? 0.25f
+         : b == 8 ? 1.0f / 12.0f
+         : b == 9 ? 1.0f / 18.0f
+         : b <= 12 ? 0.0625f
+         : b == 13 ? 0.125f
+                   : 0.0625f;
 }
 
-struct RelaxRates15 {
-    float w[15];
+// omega_beta / k_beta per beta, in the value type V.
+template <typename V>
+struct Rates15 {
+    V w[15];
 };
 
-// Source S_alpha = sum_beta K_beta(e_alpha) m^s_beta / D_beta with the
-// projections m^s_beta of App. G.
-__device__ __forceinline__ void source15(float Fx, float Fy, float Fz, float ux, float uy,
-                                         float uz, float (&S)[15]) {
-    float m[15];
-    m[0] = 0.0f;
+// Projections m^s_beta = <K_beta|S> of the source (App. G), beta = 0..14.
+template <typename V>
+__device__ __forceinline__ void source_projections15(V Fx, V Fy, V Fz, V ux, V uy, V uz,
+                                                     V (&m)[15]) {
+    const V two = splat<V>(2.0f), three = splat<V>(3.0f), five = splat<V>(5.0f);
+    const V m4 = splat<V>(-4.0f), m13 = splat<V>(-13.0f);
+    m[0] = splat<V>(0.0f);
     m[1] = Fx;
     m[2] = Fy;
     m[3] = Fz;
-    m[4] = Fx * uy + Fy * ux;
-    m[5] = Fx * uz + Fz * ux;
-    m[6] = Fy * uz + Fz * uy;
-    const float fux = Fx * ux, fuy = Fy * uy, fuz = Fz * uz;
-    m[7] = 2.0f * (fux - fuy);
-    m[8] = 2.0f * (fux + fuy - 2.0f * fuz);
-    m[9] = 2.0f * (fux + fuy + fuz);
-    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-    m[10] = 5.0f * (Fx * (3.0f * ux2 + uy2 + uz2) + 2.0f * ux * (fuy + fuz)) - 13.0f * Fx;
-    m[11] = 5.0f * (Fy * (ux2 + 3.0f * uy2 + uz2) + 2.0f * uy * (fux + fuz)) - 13.0f * Fy;
-    m[12] = 5.0f * (Fz * (ux2 + uy2 + 3.0f * uz2) + 2.0f * uz * (fux + fuy)) - 13.0f * Fz;
-    m[13] = Fx * uy * uz + Fy * ux * uz + Fz * ux * uy;
-    m[14] = 20.0f * (fux * (3.0f * (uy2 + uz2) - 4.0f) + fuy * (3.0f * (ux2 + uz2) - 4.0f) +
-                     fuz * (3.0f * (ux2 + uy2) - 4.0f));
-    static_for<15>([&](auto ia) {
-        constexpr int a = decltype(ia)::value;
-        float s = 0.0f;
-        static_for<15>([&](auto ib) {
-            constexpr int b = decltype(ib)::value;
-            constexpr int k = k15(b, a);
-            if constexpr (b >= 1 && k != 0) {
-                constexpr float c = float(k) / float(d15(b));
-                s = fmaf(c, m[b], s);
-            }
-        });
-        S[a] = s;
-    });
+    m[4] = vfma(Fx, uy, Fy * ux);
+    m[5] = vfma(Fx, uz, Fz * ux);
+    m[6] = vfma(Fy, uz, Fz * uy);
+    const V fux = Fx * ux, fuy = Fy * uy, fuz = Fz * uz;
+    m[7] = two * (fux - fuy);
+    m[8] = two * ((fux + fuy) - two * fuz);
+    m[9] = two * (fux + fuy + fuz);
+    const V ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    m[10] = vfma(five, vfma(Fx, vfma(three, ux2, uy2 + uz2), two * ux * (fuy + fuz)), m13 * Fx);
+    m[11] = vfma(five, vfma(Fy, vfma(three, uy2, ux2 + uz2), two * uy * (fux + fuz)), m13 * Fy);
+    m[12] = vfma(five, vfma(Fz, vfma(three, uz2, ux2 + uy2), two * uz * (fux + fuy)), m13 * Fz);
+    m[13] = vfma(Fx, uy * uz, vfma(Fy, ux * uz, Fz * (ux * uy)));
+    m[14] = splat<V>(20.0f) * vfma(fux, vfma(three, uy2 + uz2, m4),
+                                   vfma(fuy, vfma(three, ux2 + uz2, m4),
+                                        fuz * vfma(three, ux2 + uy2, m4)));
 }
 
-// The cascade on deviation raw moments.  dk*: raw moments of the deviations
-// f - w; returns g[4..14].
-__device__ __forceinline__ void kernels15(const float (&f)[15], float Fx, float Fy, float Fz,
-                                          const RelaxRates15 &r, float &ux, float &uy, float &uz,
-                                          float (&g)[15]) {
-    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
-    float kxy = 0.f, kxz = 0.f, kyz = 0.f, kxx = 0.f, kyy = 0.f, kzz = 0.f;
-    float kxyy = 0.f, kxxy = 0.f, kxxz = 0.f, kxyz = 0.f, kxxyy = 0.f;
+// The cascade on deviation raw moments; returns u and g[4..14].  The rates
+// carry the App. G prefactors: r.w[beta] = omega_beta / k_beta.
+template <typename V>
+__device__ __forceinline__ void kernels15(const V (&f)[15], V Fx, V Fy, V Fz, const Rates15<V> &r,
+                                          V &ux, V &uy, V &uz, V (&g)[15]) {
+    const V zero = splat<V>(0.0f);
+    V drho = zero, jx = zero, jy = zero, jz = zero;
+    V kxy = zero, kxz = zero, kyz = zero, kxx = zero, kyy = zero, kzz = zero;
+    V kxyy = zero, kxxy = zero, kxxz = zero, kxyz = zero, kxxyy = zero;
+    // signed sums of the deviations over the index sets of App. G
     static_for<15>([&](auto ia) {
         constexpr int a = decltype(ia)::value;
         constexpr int x = q15_e(a, 0), y = q15_e(a, 1), z = q15_e(a, 2);
-        const float v = f[a];
-        drho += v;
-        if constexpr (x != 0) {
-            jx += x * v;
-            kxx += v;
+        const V v = f[a];
+        drho = drho + v;
+        if constexpr (x > 0) jx = jx + v;
+        if constexpr (x < 0) jx = jx - v;
+        if constexpr (y > 0) jy = jy + v;
+        if constexpr (y < 0) jy = jy - v;
+        if constexpr (z > 0) jz = jz + v;
+        if constexpr (z < 0) jz = jz - v;
+        if constexpr (x != 0) kxx = kxx + v;
+        if constexpr (y != 0) kyy = kyy + v;
+        if constexpr (z != 0) kzz = kzz + v;
+        if constexpr (x * y * z != 0) {  // corners
+            kxxyy = kxxyy + v;
+            if constexpr (x * y > 0) kxy = kxy + v;
+            if constexpr (x * y < 0) kxy = kxy - v;
+            if constexpr (x * z > 0) kxz = kxz + v;
+            if constexpr (x * z < 0) kxz = kxz - v;
+            if constexpr (y * z > 0) kyz = kyz + v;
+            if constexpr (y * z < 0) kyz = kyz - v;
+            if constexpr (x > 0) kxyy = kxyy + v;
+            if constexpr (x < 0) kxyy = kxyy - v;
+            if constexpr (y > 0) kxxy = kxxy + v;
+            if constexpr (y < 0) kxxy = kxxy - v;
+            if constexpr (z > 0) kxxz = kxxz + v;
+            if constexpr (z < 0) kxxz = kxxz - v;
+            if constexpr (x * y * z > 0) kxyz = kxyz + v;
+            if constexpr (x * y * z < 0) kxyz = kxyz - v;
         }
-        if constexpr (y != 0) {
-            jy += y * v;
-            kyy += v;
-        }
-        if constexpr (z != 0) {
-            jz += z * v;
-            kzz += v;
-        }
-        if constexpr (x * y != 0) {
-            kxy += (x * y) * v;
-            kxyy += x * v;
-            kxxy += y * v;
-            kxxyy += v;
-        }
-        if constexpr (x * z != 0) {
-            kxz += (x * z) * v;
-            kxxz += z * v;
-        }
-        if constexpr (y * z != 0) kyz += (y * z) * v;
-        if constexpr (x * y * z != 0) kxyz += (x * y * z) * v;
     });
-    const float rho = 1.0f + drho;
-    const float inv_rho = 1.0f / rho;
-    ux = (jx + 0.5f * Fx) * inv_rho;
-    uy = (jy + 0.5f * Fy) * inv_rho;
-    uz = (jz + 0.5f * Fz) * inv_rho;
-    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const V one = splat<V>(1.0f), half = splat<V>(0.5f), two = splat<V>(2.0f);
+    const V three = splat<V>(3.0f), eighth = splat<V>(0.125f);
+    const V rho = one + drho;
+    const V inv_rho = vrcp(rho);
+    ux = vfma(half, Fx, jx) * inv_rho;
+    uy = vfma(half, Fy, jy) * inv_rho;
+    uz = vfma(half, Fz, jz) * inv_rho;
+    const V ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const V uxy = ux * uy, uxz = ux * uz, uyz = uy * uz;
     // raw source moments (App. C); eta' = kappa' + sigma' as deviations
-    const float sx = Fx, sy = Fy, sz = Fz;
-    const float exy = kxy + (Fx * uy + Fy * ux);
-    const float exz = kxz + (Fx * uz + Fz * ux);
-    const float eyz = kyz + (Fy * uz + Fz * uy);
-    const float exx = kxx + 2.0f * Fx * ux;
-    const float eyy = kyy + 2.0f * Fy * uy;
-    const float ezz = kzz + 2.0f * Fz * uz;
-    const float exyy = kxyy + (Fx * uy2 + 2.0f * Fy * uy * ux);
-    const float exxy = kxxy + (Fy * ux2 + 2.0f * Fx * ux * uy);
-    const float exxz = kxxz + (Fz * ux2 + 2.0f * Fx * ux * uz);
-    const float exyz = kxyz + (Fx * uy * uz + Fy * ux * uz + Fz * ux * uy);
-    const float exxyy = kxxyy + (2.0f * Fx * ux * uy2 + 2.0f * Fy * uy * ux2);
-    const float third = 1.0f / 3.0f;
-    const float Exx = third + exx, Eyy = third + eyy;  // full eta'_xx, eta'_yy
+    const V sx = Fx, sy = Fy, sz = Fz;
+    const V fux = Fx * ux, fuy = Fy * uy, fuz = Fz * uz;
+    const V exy = kxy + vfma(Fx, uy, Fy * ux);
+    const V exz = kxz + vfma(Fx, uz, Fz * ux);
+    const V eyz = kyz + vfma(Fy, uz, Fz * uy);
+    const V exx = vfma(two, fux, kxx);
+    const V eyy = vfma(two, fuy, kyy);
+    const V ezz = vfma(two, fuz, kzz);
+    const V exyy = kxyy + vfma(Fx, uy2, two * fuy * ux);
+    const V exxy = kxxy + vfma(Fy, ux2, two * fux * uy);
+    const V exxz = kxxz + vfma(Fz, ux2, two * fux * uz);
+    const V exyz = kxyz + vfma(Fx, uyz, vfma(Fy, uxz, Fz * uxy));
+    const V exxyy = kxxyy + two * vfma(fux, uy2, fuy * ux2);
+    const V third = splat<V>(1.0f / 3.0f);
+    const V Exx = third + exx, Eyy = third + eyy;  // full eta'_xx, eta'_yy
 
+    const V s_u = vfma(sx, ux, vfma(sy, uy, sz * uz));
 #pragma unroll
-    for (int b = 0; b < 15; ++b) g[b] = 0.0f;
-    g[4] = r.w[4] * 0.125f * (-exy + rho * ux * uy + 0.5f * (sx * uy + sy * ux));
-    g[5] = r.w[5] * 0.125f * (-exz + rho * ux * uz + 0.5f * (sx * uz + sz * ux));
-    g[6] = r.w[6] * 0.125f * (-eyz + rho * uy * uz + 0.5f * (sy * uz + sz * uy));
-    g[7] = r.w[7] * 0.25f * (-(exx - eyy) + rho * (ux2 - uy2) + (sx * ux - sy * uy));
-    g[8] = r.w[8] * (1.0f / 12.0f) *
-           (-(exx + eyy - 2.0f * ezz) + rho * (ux2 + uy2 - 2.0f * uz2) +
-            (sx * ux + sy * uy - 2.0f * sz * uz));
-    // -(eta'_xx + eta'_yy + eta'_zz) + rho = -(dev sum) - 1 + rho
-    g[9] = r.w[9] * (1.0f / 18.0f) *
-           (-(exx + eyy + ezz) + rho * (ux2 + uy2 + uz2) + (sx * ux + sy * uy + sz * uz) + drho);
-    g[10] = r.w[10] * 0.0625f *
-                (-exyy + 2.0f * uy * exy + ux * Eyy - 2.0f * rho * ux * uy2 - 0.5f * sx * uy2 -
-                 sy * uy * ux) +
-            uy * g[4] + 0.125f * ux * (-g[7] + g[8] + 3.0f * g[9]);
-    g[11] = r.w[11] * 0.0625f *
-                (-exxy + 2.0f * ux * exy + uy * Exx - 2.0f * rho * ux2 * uy - 0.5f * sy * ux2 -
-                 sx * ux * uy) +
-            ux * g[4] + 0.125f * uy * (g[7] + g[8] + 3.0f * g[9]);
-    g[12] = r.w[12] * 0.0625f *
-                (-exxz + 2.0f * ux * exz + uz * Exx - 2.0f * rho * ux2 * uz - 0.5f * sz * ux2 -
-                 sx * ux * uz) +
-            ux * g[5] + 0.125f * uz * (g[7] + g[8] + 3.0f * g[9]);
-    g[13] = r.w[13] * 0.125f *
-                (-exyz + ux * eyz + uy * exz + uz * exy - 2.0f * rho * ux * uy * uz -
-                 0.5f * (sx * uy * uz + sy * ux * uz + sz * ux * uy)) +
-            uz * g[4] + uy * g[5] + ux * g[6];
+    for (int b = 0; b < 4; ++b) g[b] = zero;
+    g[4] = r.w[4] * (vfma(rho, uxy, half * vfma(sx, uy, sy * ux)) - exy);
+    g[5] = r.w[5] * (vfma(rho, uxz, half * vfma(sx, uz, sz * ux)) - exz);
+    g[6] = r.w[6] * (vfma(rho, uyz, half * vfma(sy, uz, sz * uy)) - eyz);
+    g[7] = r.w[7] * (vfma(rho, ux2 - uy2, fux - fuy) - (exx - eyy));
+    g[8] = r.w[8] * (vfma(rho, (ux2 + uy2) - two * uz2, (fux + fuy) - two * fuz) -
+                     ((exx + eyy) - two * ezz));
+    // -(eta'_xx + eta'_yy + eta'_zz) + rho = -(deviation sum) - 1 + rho
+    g[9] = r.w[9] * (vfma(rho, ux2 + uy2 + uz2, s_u + drho) - (exx + eyy + ezz));
+    g[10] = vfma(r.w[10],
+                 vfma(two * uy, exy, ux * Eyy) -
+                     vfma(two * rho * ux, uy2, vfma(half * sx, uy2, sy * uy * ux)) - exyy,
+                 vfma(uy, g[4], eighth * ux * vfma(three, g[9], g[8] - g[7])));
+    g[11] = vfma(r.w[11],
+                 vfma(two * ux, exy, uy * Exx) -
+                     vfma(two * rho * ux2, uy, vfma(half * sy, ux2, sx * uxy)) - exxy,
+                 vfma(ux, g[4], eighth * uy * vfma(three, g[9], g[8] + g[7])));
+    g[12] = vfma(r.w[12],
+                 vfma(two * ux, exz, uz * Exx) -
+                     vfma(two * rho * ux2, uz, vfma(half * sz, ux2, sx * uxz)) - exxz,
+                 vfma(ux, g[5], eighth * uz * vfma(three, g[9], g[8] + g[7])));
+    g[13] = vfma(r.w[13],
+                 vfma(ux, eyz, vfma(uy, exz, uz * exy)) -
+                     vfma(two * rho, ux * uyz, half * vfma(sx, uyz, vfma(sy, uxz, sz * uxy))) -
+                     exyz,
+                 vfma(uz, g[4], vfma(uy, g[5], ux * g[6])));
     // post-collision kappa~_xx, kappa~_yy as deviations from 1/3
-    const float dkx = exx + 2.0f * g[7] + 2.0f * g[8] + 6.0f * g[9] - rho * ux2 - Fx * ux;
-    const float dky = eyy - 2.0f * g[7] + 2.0f * g[8] + 6.0f * g[9] - rho * uy2 - Fy * uy;
+    const V six = splat<V>(6.0f);
+    const V dkx = vfma(six, g[9], exx + two * (g[7] + g[8])) - vfma(rho, ux2, fux);
+    const V dky = vfma(six, g[9], eyy + two * (g[8] - g[7])) - vfma(rho, uy2, fuy);
     // -eta'_xxyy + kappa~_xx kappa~_yy = -dev_xxyy + (dkx + dky)/3 + dkx dky
-    g[14] = r.w[14] * 0.0625f *
-                (-exxyy + 2.0f * ux * exyy + 2.0f * uy * exxy - ux2 * Eyy - uy2 * Exx -
-                 4.0f * ux * uy * exy + (dkx + dky) * third + dkx * dky +
-                 3.0f * rho * ux2 * uy2 + sx * ux * uy2 + sy * uy * ux2) -
-            2.0f * ux * uy * g[4] + 0.125f * (ux2 - uy2) * g[7] - 0.125f * (ux2 + uy2) * g[8] +
-            (-0.375f * (ux2 + uy2) - 0.5f) * g[9] + 2.0f * ux * g[10] + 2.0f * uy * g[11];
+    const V br14 = vfma(two * ux, exyy, two * uy * exxy) - vfma(ux2, Eyy, uy2 * Exx) -
+                   splat<V>(4.0f) * uxy * exy + vfma(dkx + dky, third, dkx * dky) +
+                   vfma(three * rho, ux2 * uy2, vfma(sx, ux * uy2, sy * uy * ux2)) - exxyy;
+    g[14] = vfma(r.w[14], br14,
+                 vfma(splat<V>(-2.0f) * uxy, g[4],
+                      vfma(eighth * (ux2 - uy2), g[7],
+                           vfma(splat<V>(-0.125f) * (ux2 + uy2), g[8],
+                                vfma(vfma(splat<V>(-0.375f), ux2 + uy2, splat<V>(-0.5f)), g[9],
+                                     two * vfma(ux, g[10], uy * g[11]))))));
 }
 
-// One cell: deviations in, post-collision deviations out.
-__device__ __forceinline__ void collide15(float (&f)[15], float Fx, float Fy, float Fz,
-                                          const RelaxRates15 &r) {
-    float g[15], S[15], ux, uy, uz;
-    kernels15(f, Fx, Fy, Fz, r, ux, uy, uz, g);
-    source15(Fx, Fy, Fz, ux, uy, uz, S);
-    static_for<15>([&](auto ia) {
-        constexpr int a = decltype(ia)::value;
-        float s = f[a] + S[a];
-        static_for<15>([&](auto ib) {
-            constexpr int b = decltype(ib)::value;
-            constexpr int k = k15(b, a);
-            if constexpr (b >= 4 && k != 0) s = fmaf(float(k), g[b], s);
-        });
-        f[a] = s;
+// Add K.g (and with kSource the source S of App. G, from its projections m)
+// to the deviations f, by sign patterns (see the file comment).
+template <typename V, bool kSource>
+__device__ __forceinline__ void update15(V (&f)[15], const V (&g)[15], const V (&m)[15]) {
+    const V two = splat<V>(2.0f), eight = splat<V>(8.0f), m8 = splat<V>(-8.0f);
+    // rest: K.g = -2 g9 + 32 g14;  S = (3 m0 - 5 m9 + m14) / 45
+    V rest = vfma(splat<V>(32.0f), g[14], splat<V>(-2.0f) * g[9]);
+    // axis pairs: even part E, odd part O
+    const V g914 = vfma(eight, g[14], g[9]);
+    V Ex = (g[7] + g[8]) - g914;
+    V Ey = (g[8] - g[7]) - g914;
+    V Ez = splat<V>(-2.0f) * g[8] - g914;
+    V Ox = m8 * g[10], Oy = m8 * g[11], Oz = m8 * g[12];
+    // corners: c0 + sx cx + sy cy + sz cz + sx sy cxy + sx sz cxz + sy sz cyz
+    //          + sx sy sz cxyz
+    V c0 = vfma(two, g[14], g[9]);
+    V cx = two * g[10], cy = two * g[11], cz = two * g[12];
+    V cxy = g[4], cxz = g[5], cyz = g[6], cxyz = g[13];
+    if constexpr (kSource) {
+        const V i180 = splat<V>(1.0f / 180.0f), i720 = splat<V>(1.0f / 720.0f);
+        rest = vfma(splat<V>(1.0f / 45.0f), vfma(splat<V>(-5.0f), m[9], m[14]), rest);
+        const V ev = vfma(splat<V>(10.0f), m[9], m[14]);
+        Ex = vfma(i180, vfma(splat<V>(45.0f), m[7], splat<V>(15.0f) * m[8]) - ev, Ex);
+        Ey = vfma(i180, vfma(splat<V>(-45.0f), m[7], splat<V>(15.0f) * m[8]) - ev, Ey);
+        Ez = vfma(i180, splat<V>(-30.0f) * m[8] - ev, Ez);
+        Ox = vfma(i180, vfma(splat<V>(18.0f), m[1], splat<V>(-9.0f) * m[10]), Ox);
+        Oy = vfma(i180, vfma(splat<V>(18.0f), m[2], splat<V>(-9.0f) * m[11]), Oy);
+        Oz = vfma(i180, vfma(splat<V>(18.0f), m[3], splat<V>(-9.0f) * m[12]), Oz);
+        c0 = vfma(i720, vfma(splat<V>(40.0f), m[9], m[14]), c0);
+        cx = vfma(i720, vfma(splat<V>(72.0f), m[1], splat<V>(9.0f) * m[10]), cx);
+        cy = vfma(i720, vfma(splat<V>(72.0f), m[2], splat<V>(9.0f) * m[11]), cy);
+        cz = vfma(i720, vfma(splat<V>(72.0f), m[3], splat<V>(9.0f) * m[12]), cz);
+        const V eighth = splat<V>(0.125f);
+        cxy = vfma(eighth, m[4], cxy);
+        cxz = vfma(eighth, m[5], cxz);
+        cyz = vfma(eighth, m[6], cyz);
+        cxyz = vfma(eighth, m[13], cxyz);
+    }
+    f[0] = f[0] + rest;
+    f[1] = f[1] + (Ex + Ox);  // (+1, 0, 0)
+    f[2] = f[2] + (Ex - Ox);  // (-1, 0, 0)
+    f[3] = f[3] + (Ey + Oy);
+    f[4] = f[4] + (Ey - Oy);
+    f[5] = f[5] + (Ez + Oz);
+    f[6] = f[6] + (Ez - Oz);
+    // butterflies over sz, then sy, then sx (index 0: sz = +1, 1: sz = -1)
+    V A[2], Bx[2], By[2], Bxy[2];
+    A[0] = c0 + cz;
+    A[1] = c0 - cz;
+    Bx[0] = cx + cxz;
+    Bx[1] = cx - cxz;
+    By[0] = cy + cyz;
+    By[1] = cy - cyz;
+    Bxy[0] = cxy + cxyz;
+    Bxy[1] = cxy - cxyz;
+    static_for<8>([&](auto ic) {
+        constexpr int a = 7 + decltype(ic)::value;
+        constexpr int x = q15_e(a, 0), y = q15_e(a, 1), z = q15_e(a, 2);
+        constexpr int k = z > 0 ? 0 : 1;
+        const V P = y > 0 ? A[k] + By[k] : A[k] - By[k];
+        const V R = y > 0 ? Bx[k] + Bxy[k] : Bx[k] - Bxy[k];
+        f[a] = f[a] + (x > 0 ? P + R : P - R);
     });
+}
+
+// One cell (or a pair, V = f2): deviations in, post-collision deviations
+// out.  with_source = false (no force anywhere) skips S.
+template <typename V>
+__device__ __forceinline__ void collide15(V (&f)[15], V Fx, V Fy, V Fz, const Rates15<V> &r,
+                                          bool with_source) {
+    V g[15], ux, uy, uz;
+    kernels15(f, Fx, Fy, Fz, r, ux, uy, uz, g);
+    V m[15];
+    if (with_source) {
+        source_projections15(Fx, Fy, Fz, ux, uy, uz, m);
+        update15<V, true>(f, g, m);
+    } else {
+        update15<V, false>(f, g, m);
+    }
 }
 
 // Deviations of f = f^at(rho, u) - S/2: one collision with every omega = 1
@@ -220,23 +299,23 @@ __device__ __forceinline__ void equilibrium15(float drho, float ux, float uy, fl
         const float eu = cx * ux + cy * uy + cz * uz;
         f[a] = float(weight<15>(a)) * (drho + 3.0f * rho * eu);
     });
-    RelaxRates15 ones;
+    Rates15<float> ones;
 #pragma unroll
-    for (int b = 0; b < 15; ++b) ones.w[b] = 1.0f;
-    float g[15], ux0, uy0, uz0;
-    kernels15(f, 0.0f, 0.0f, 0.0f, ones, ux0, uy0, uz0, g);
-    float S[15];
-    source15(Fx, Fy, Fz, ux, uy, uz, S);
-    static_for<15>([&](auto ia) {
-        constexpr int a = decltype(ia)::value;
-        float s = f[a];
-        static_for<15>([&](auto ib) {
-            constexpr int b = decltype(ib)::value;
-            constexpr int k = k15(b, a);
-            if constexpr (b >= 4 && k != 0) s = fmaf(float(k), g[b], s);
-        });
-        f[a] = s - 0.5f * S[a];
-    });
+    for (int b = 0; b < 15; ++b) ones.w[b] = k15_inv(b);
+    float g[15], ux0, uy0, uz0, m[15];
+    kernels15<float>(f, 0.0f, 0.0f, 0.0f, ones, ux0, uy0, uz0, g);
+    update15<float, false>(f, g, m);
+    // minus half the source at (F, u): the update with g = 0 adds S alone
+    float S[15], zg[15];
+#pragma unroll
+    for (int a = 0; a < 15; ++a) {
+        S[a] = 0.0f;
+        zg[a] = 0.0f;
+    }
+    source_projections15<float>(Fx, Fy, Fz, ux, uy, uz, m);
+    update15<float, true>(S, zg, m);
+#pragma unroll
+    for (int a = 0; a < 15; ++a) f[a] = f[a] - 0.5f * S[a];
 }
 
 }  // namespace lbm

@@ -17,6 +17,7 @@ struct StepArgs {
     float w[27];           // relaxation rates omega_beta (first Q used)
     float F[3];            // uniform body force
     const float *Ffield;   // per-cell force [3][nz][ny][nx] or nullptr
+    int has_force;         // 0: no force anywhere (the source term vanishes)
 };
 
 // Launch geometry shared by the per-cell kernels: blocks of 128 threads laid
@@ -55,7 +56,7 @@ struct Rates<27> {
 };
 template <>
 struct Rates<15> {
-    using type = RelaxRates15;
+    using type = Rates15<float>;
 };
 
 __device__ __forceinline__ Rates27<float> load_rates27(const StepArgs &a) {
@@ -76,25 +77,25 @@ __device__ __forceinline__ Rates27<float> load_rates<27>(const StepArgs &a) {
     return load_rates27(a);
 }
 template <>
-__device__ __forceinline__ RelaxRates15 load_rates<15>(const StepArgs &a) {
-    RelaxRates15 r;
+__device__ __forceinline__ Rates15<float> load_rates<15>(const StepArgs &a) {
+    Rates15<float> r;
 #pragma unroll
-    for (int b = 0; b < 15; ++b) r.w[b] = a.w[b];
+    for (int b = 0; b < 15; ++b) r.w[b] = a.w[b] * k15_inv(b);
     return r;
 }
 
 template <int Q>
 __device__ __forceinline__ void collide(float (&f)[Q], float Fx, float Fy, float Fz,
-                                        const typename Rates<Q>::type &r);
+                                        const typename Rates<Q>::type &r, bool has_force);
 template <>
 __device__ __forceinline__ void collide<27>(float (&f)[27], float Fx, float Fy, float Fz,
-                                            const Rates27<float> &r) {
+                                            const Rates27<float> &r, bool) {
     collide27<float>(f, Fx, Fy, Fz, r);
 }
 template <>
 __device__ __forceinline__ void collide<15>(float (&f)[15], float Fx, float Fy, float Fz,
-                                            const RelaxRates15 &r) {
-    collide15(f, Fx, Fy, Fz, r);
+                                            const Rates15<float> &r, bool has_force) {
+    collide15<float>(f, Fx, Fy, Fz, r, has_force);
 }
 
 template <int Q>
@@ -177,9 +178,11 @@ struct Pair<__nv_bfloat16> {
     }
 };
 
-// Relaxation rates pre-broadcast to both lanes, built on the host.
+// Relaxation rates pre-broadcast to both lanes, built on the host:
+// D3Q27 omega, -omega, 1 - omega; D3Q15 omega / k_beta.
 struct PackedRates {
     unsigned long long w[27], nw[27], omw[27];
+    unsigned long long w15[15];
 };
 
 __device__ __forceinline__ Rates27<f2> load_rates_packed(const PackedRates &p) {
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const Ste
     const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
     cell_force(a, dense_index(a.g, x, y, z), N, Fx, Fy, Fz);
     const typename Rates<Q>::type r = load_rates<Q>(a);
-    collide<Q>(f, Fx, Fy, Fz, r);
+    collide<Q>(f, Fx, Fy, Fz, r, a.has_force != 0);
 #pragma unroll
     for (int q = 0; q < Q; ++q) store_dev<Q, T>(io.out[q] + R.own + x, q, f[q]);
 }
@@ -304,6 +307,60 @@ __global__ void __launch_bounds__(128) step2_kernel(const StepIO<T> io, const St
         const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<27>(q))) : f[q];
         Pair<T>::st2(io.out[q] + R.own + x0, v);
     }
+}
+
+// Pair gather for lattice Q: population q of cells (x0, x0 + 1) from the pull
+// sources (see step2_kernel).
+template <int Q, typename T, bool kWalls>
+__device__ __forceinline__ f2 pull_pair(const StepIO<T> &io, const Rows<kWalls> &R, int q, int x0,
+                                        int xm, int xp) {
+    const int i = ex<Q>(q), j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
+    if (kWalls && R.wall[j][k]) return Pair<T>::ld2(io.in[opposite<Q>(q)] + R.own + x0);
+    const T *row = io.in[q] + R.off[j][k];
+    if (i == 0) return Pair<T>::ld2(row + x0);
+    if (i == 1) return f2(Pair<T>::ld1(row + xm), Pair<T>::ld1(row + x0));
+    return f2(Pair<T>::ld1(row + x0 + 1), Pair<T>::ld1(row + xp));
+}
+
+// One fused D3Q15 step, two neighbouring cells per thread in packed f32x2
+// arithmetic (nx even); loads and stores as in step2_kernel.
+template <typename T, bool kWalls>
+__global__ void __launch_bounds__(128) step2_q15_kernel(const StepIO<T> io, const StepArgs a,
+                                                        const PackedRates pr) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    const int x0 = 2 * t;
+    if (x0 >= a.g.nx || y >= a.g.ny) return;
+    const Rows<kWalls> R = pull_rows<kWalls>(a.g, y, z);
+    const int xm = (x0 == 0) ? a.g.nx - 1 : x0 - 1;
+    const int xp = (x0 + 2 == a.g.nx) ? 0 : x0 + 2;
+    f2 f[15];
+    static_for<15>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        const f2 v = pull_pair<15, T, kWalls>(io, R, q, x0, xm, xp);
+        f[q] = Storage<T>::kScaled ? v * f2(float(weight<15>(q))) : v;
+    });
+    f2 Fx, Fy, Fz;
+    if (a.Ffield) {
+        const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
+        const long long c = dense_index(a.g, x0, y, z);
+        Fx = f2(__ldg(a.Ffield + c), __ldg(a.Ffield + c + 1));
+        Fy = f2(__ldg(a.Ffield + N + c), __ldg(a.Ffield + N + c + 1));
+        Fz = f2(__ldg(a.Ffield + 2 * N + c), __ldg(a.Ffield + 2 * N + c + 1));
+    } else {
+        Fx = f2(a.F[0]);
+        Fy = f2(a.F[1]);
+        Fz = f2(a.F[2]);
+    }
+    Rates15<f2> r;
+#pragma unroll
+    for (int b = 0; b < 15; ++b) r.w[b] = f2(pr.w15[b]);
+    collide15<f2>(f, Fx, Fy, Fz, r, a.has_force != 0);
+    static_for<15>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<15>(q))) : f[q];
+        Pair<T>::st2(io.out[q] + R.own + x0, v);
+    });
 }
 
 // Initial state from FP64 density and velocity fields.
@@ -433,8 +490,15 @@ __global__ void __launch_bounds__(kRedThreads) conservation_kernel(const T *__re
 
 // Launchers.  kernels_q27.cu / kernels_q15.cu hold their explicit
 // instantiations; api.cu sees them through the extern declarations below.
+inline unsigned long long splat_bits(float v) {
+    unsigned int u;
+    memcpy(&u, &v, 4);
+    return (unsigned long long)u << 32 | u;
+}
+
 inline PackedRates packed_rates(const StepArgs &a) {
     PackedRates p;
+    for (int b = 0; b < 15; ++b) p.w15[b] = splat_bits(a.w[b] * k15_inv(b));
     for (int b = 0; b < 27; ++b) {
         const float w = a.w[b], nw = -a.w[b], omw = 1.0f - a.w[b];
         unsigned int uw, unw, uomw;
@@ -468,6 +532,18 @@ cudaError_t launch_step(const void *fin, void *fout, const StepArgs &a, cudaStre
                 step2_kernel<T, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
             else
                 step2_kernel<T, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
+            return cudaGetLastError();
+        }
+    } else {
+        if (a.g.nx % 2 == 0) {
+            Grid half = a.g;
+            half.nx = a.g.nx / 2;
+            const CellLaunch L = cell_launch(half);
+            const PackedRates pr = packed_rates(a);
+            if (walls)
+                step2_q15_kernel<T, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+            else
+                step2_q15_kernel<T, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
             return cudaGetLastError();
         }
     }

@@ -77,8 +77,8 @@ def test_one_step_from_random_state(lbm, orc, Q, bc, shape):
 
 
 @pytest.mark.parametrize("Q", [27, 15])
-def test_one_step_with_force_field(lbm, orc, Q):
-    shape = (6, 11, 35)
+@pytest.mark.parametrize("shape", [(6, 11, 35), (6, 11, 36)])  # one-cell and two-cell kernels
+def test_one_step_with_force_field(lbm, orc, Q, shape):
     f0 = W.random_field_state(shape, Q, seed=7, spread=0.3)
     om = W.random_omegas(Q, seed=8)
     F = W.rng(9).uniform(-5e-3, 5e-3, (3,) + shape)
@@ -176,8 +176,8 @@ def test_taylor_green_32cubed_100_steps(lbm, orc, Q):
 
 
 @pytest.mark.parametrize("Q", [27, 15])
-def test_walled_channel_with_force_field_matches_oracle(lbm, orc, Q):
-    shape = (9, 10, 13)
+@pytest.mark.parametrize("shape", [(9, 10, 13), (9, 10, 14)])
+def test_walled_channel_with_force_field_matches_oracle(lbm, orc, Q, shape):
     om = W.omegas(Q, 1.25)
     F = W.rng(14).uniform(-1e-4, 1e-4, (3,) + shape) + np.array([1e-4, 0, 0])[:, None, None,
                                                                               None]
