@@ -50,6 +50,8 @@ def parse():
                    help="lattice of the main measurement (profiling runs)")
     p.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                    help="storage of the main measurement (profiling runs)")
+    p.add_argument("--inplace", action="store_true",
+                   help="time the single-buffer in-place (AA) scheme as the main line")
     p.add_argument("--adjoint-only", action="store_true",
                    help="time only the adjoint workload at --size (profiling runs)")
     return p.parse_args()
@@ -165,19 +167,28 @@ def cpu_baseline(size, budget_s=15.0):
     shape = (nz_s, size, size)
     rho, u = W.taylor_green((size, size, size), u0=0.02, noise=1e-3)
     f = oracle.equilibrium(Q, rho[:nz_s], u[:, :nz_s], np.zeros(3))
-    t0 = time.perf_counter()
-    oracle.run(Q, shape, f, np.zeros(3), om, 1)
-    one = time.perf_counter() - t0
-    steps = max(1, int(budget_s / max(one, 1e-3)))
-    t0 = time.perf_counter()
-    oracle.run(Q, shape, f, np.zeros(3), om, steps)
-    dt = time.perf_counter() - t0
+    cores = oracle.max_threads()
     cells = size * size * nz_s
-    return {"value": cells * steps / dt / 1e6, "unit": UNIT, "cores": oracle.max_threads(),
+
+    def timed(nthreads, budget):
+        t0 = time.perf_counter()
+        oracle.run(Q, shape, f, np.zeros(3), om, 1, nthreads=nthreads)
+        one = time.perf_counter() - t0
+        steps = max(1, int(budget / max(one, 1e-3)))
+        t0 = time.perf_counter()
+        oracle.run(Q, shape, f, np.zeros(3), om, steps, nthreads=nthreads)
+        return steps, time.perf_counter() - t0
+
+    steps, dt = timed(cores, budget_s)
+    steps1, dt1 = timed(1, budget_s / 3)
+    oracle.run(Q, shape, f, np.zeros(3), om, 0, nthreads=cores)  # restore the thread count
+    return {"value": cells * steps / dt / 1e6, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": "%d steps of one %dx%dx%d z-slab of the %d^3 Taylor-Green+noise field "
                       "(periodic), D3Q27, tau=0.6, FP64, %.1f s" % (steps, size, size, nz_s,
-                                                                   size, dt)}
+                                                                   size, dt),
+            "single_thread": {"value": cells * steps1 / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": "%d steps of the same slab, %.1f s" % (steps1, dt1)}}
 
 
 def run_reference(args):
@@ -234,12 +245,12 @@ def run_reference(args):
     return 0
 
 
-def make_solver(lbm, Q, size, storage, tau):
+def make_solver(lbm, Q, size, storage, tau, inplace=False):
     import workloads as W
     shape = (size, size, size)
     om = W.omegas(Q, 1 / tau)
     rho, u = W.taylor_green(shape, u0=0.02, noise=1e-3)
-    S = lbm.Solver(Q, shape, om, storage=storage)
+    S = lbm.Solver(Q, shape, om, storage=storage, inplace=inplace)
     S.init_equilibrium(rho, u)
     return S, rho, u
 
@@ -389,7 +400,7 @@ def run_ours(args):
                   flush=True)
         return 0
     lat, st = args.lattice, args.storage
-    S, _, _ = make_solver(lbm, lat, size, st, 0.6)
+    S, _, _ = make_solver(lbm, lat, size, st, 0.6, inplace=args.inplace)
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -411,12 +422,15 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": per_launch * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "D3Q%d Taylor-Green+noise %d^3 periodic, tau=0.6, %s storage "
-                               "of f-w" % (lat, size, st.upper()),
-                   "cells": cells, "l2": "no flush: inputs larger than L2 (2 x %.1f GB state)"
-                   % (alg_bytes / 2 / 1e9), "parallelism": "replicas" if world > 1 else "1 GPU"},
+                               "of f-w%s" % (lat, size, st.upper(),
+                                             ", in-place (AA) streaming" if args.inplace else ""),
+                   "cells": cells, "l2": "no flush: inputs larger than L2 (%s%.1f GB state)"
+                   % ("" if args.inplace else "2 x ", alg_bytes / 2 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": ncu_traffic(size) if (lat, st) == (27, "f32") else None,
+                     "traffic": ncu_traffic(size) if (lat, st, args.inplace) == (27, "f32", False)
+                     else None,
                      "peak_source": "%s hbm_gbs (copy), %d B/cell algorithmic" % (
                          peak_kind, bpc)},
         "gpu_launches": args.steps,
@@ -448,6 +462,19 @@ def run_ours(args):
             del S
             torch.cuda.empty_cache()
         result["storage_512"] = s16
+        aa = {}
+        for n, st in ((size, "f32"), (512, "f32"), (512, "f16")):
+            S, _, _ = make_solver(lbm, 27, n, st, 0.6, inplace=True)
+            t = time_steps(torch, S, 200 if n == size else 100, 6)
+            k = 200 if n == size else 100
+            bpc = BYTES_PER_CELL[("q27", st)]
+            aa["%d_%s" % (n, st)] = {"mlups": n**3 * k / t / 1e6,
+                                      "GB/s": bpc * n**3 * k / t / 1e9,
+                                      "frac": bpc * n**3 * k / t / 1e9 / peak,
+                                      "state_GB": bpc / 2 * n**3 / 1e9}
+            del S
+            torch.cuda.empty_cache()
+        result["inplace_aa"] = aa
         result["adjoint"] = adjoint_timing(torch, lbm, 128)
         torch.cuda.empty_cache()
         result["cpu_baseline"] = cpu_baseline(size)

@@ -69,6 +69,23 @@ typedef enum {
 #define LBM_WALL_Y 1u
 #define LBM_WALL_Z 2u
 
+/* bc_flags of lbm_create: single-buffer in-place streaming (the "AA"
+ * access pattern; not in the paper, which states the update with separate
+ * collision and streaming steps, Eqs. cascadedcollision1 and
+ * cascadedstreaming1).  The context then works on ONE state buffer:
+ * lbm_bind takes f_b = NULL.  Steps alternate between two kernels: the
+ * first collides every cell in place and stores its post-collision values
+ * in the opposite slots of the same cell; the second reads them from the
+ * upstream neighbours, collides and writes the results to the downstream
+ * neighbours' slots (bounce-back walls as in the two-buffer scheme).  Every
+ * thread reads and writes the same locations, so no second buffer is needed
+ * and each step moves the same bytes as a two-buffer step.  The results are
+ * bit-identical to the two-buffer scheme.  Requires nx even.
+ * lbm_current_state returns NULL and lbm_step_into and lbm_adjoint_step
+ * return LBM_EUNSUPPORTED for such a context (their buffers hold two-buffer
+ * states). */
+#define LBM_INPLACE 4u
+
 typedef struct lbm_ctx lbm_ctx;
 
 /* Create a solver context for one grid.
@@ -82,7 +99,8 @@ typedef struct lbm_ctx lbm_ctx;
  *            nu = (1/omega - 1/2)/3 (end of Sec. 7; App. G).
  *   force    host, 3 values: the uniform body force F (lattice units); used
  *            when no force field is bound.  NULL means zero.
- *   bc_flags OR of LBM_WALL_Y / LBM_WALL_Z (0: fully periodic).
+ *   bc_flags OR of LBM_WALL_Y / LBM_WALL_Z (0: fully periodic), optionally
+ *            with LBM_INPLACE (then nx must be even).
  *   storage  an lbm_storage value.
  *   out      receives the context (set to NULL on error).
  * Errors: LBM_EINVAL, LBM_ENOMEM (context allocation), LBM_ECUDA (no usable
@@ -106,6 +124,7 @@ int lbm_row_pitch(const lbm_ctx *ctx);
 /* Attach the caller's two state buffers (device, lbm_state_bytes each,
  * 256-byte aligned, not overlapping) and an optional per-cell force field
  * force_field (device, FP32 [3][nz][ny][nx], NULL = the uniform force).
+ * A context created with LBM_INPLACE takes one buffer: f_b must be NULL.
  * The buffers' contents are undefined until lbm_init_equilibrium or
  * lbm_set_state.  Rebinding is allowed between steps.
  * Errors: LBM_EINVAL (null, misaligned or equal buffers). */
@@ -142,7 +161,8 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const double *f, void *stream);
 lbm_status lbm_get_state(const lbm_ctx *ctx, double *f, void *stream);
 
 /* Advance nsteps >= 0 fused collide-and-stream steps (Eqs. cascadedcollision1
- * and cascadedstreaming1), one kernel launch per step on `stream`.
+ * and cascadedstreaming1), one kernel launch per step on `stream` (with
+ * LBM_INPLACE, alternately the in-place and the neighbour kernel).
  * Errors: LBM_ESTATE (not bound), LBM_EINVAL (nsteps < 0), LBM_ECUDA. */
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps, void *stream);
 
@@ -175,7 +195,8 @@ const void *lbm_current_state(const lbm_ctx *ctx);
 /* One collide-and-stream step from the state in f_in to f_out (device,
  * lbm_state_bytes each, 256-byte aligned, not overlapping; any buffers, not
  * only the bound pair, e.g. a checkpoint ring).  The bound pair and the
- * current state are untouched.  Errors: LBM_EINVAL, LBM_ECUDA. */
+ * current state are untouched.  Errors: LBM_EINVAL, LBM_EUNSUPPORTED
+ * (LBM_INPLACE context), LBM_ECUDA. */
 lbm_status lbm_step_into(lbm_ctx *ctx, const void *f_in, void *f_out, void *stream);
 
 /* Adjoint of one step taken from the state f_t (a state buffer holding the
@@ -187,12 +208,13 @@ lbm_status lbm_step_into(lbm_ctx *ctx, const void *f_in, void *f_out, void *stre
  * (device FP32 [3][nz][ny][nx], accumulated; the force of step t is the
  * bound force field or the uniform force).  lam_next, lam_out: device FP32
  * adjoint fields (lbm_adjoint_bytes, 16-byte aligned, distinct).
- * Errors: LBM_EINVAL, LBM_EUNSUPPORTED (D3Q15), LBM_ECUDA. */
+ * Errors: LBM_EINVAL, LBM_EUNSUPPORTED (D3Q15, LBM_INPLACE), LBM_ECUDA. */
 lbm_status lbm_adjoint_step(lbm_ctx *ctx, const void *f_t, const float *lam_next,
                             float *lam_out, float *dJdF, void *stream);
 
-/* Kinetic energy J = sum_x rho |u|^2 / 2 of the state in f (a state buffer;
- * NULL = the current state), u with the +F/2 shift; per-cell values in
+/* Kinetic energy J = sum_x rho |u|^2 / 2 of the state in f (a state buffer
+ * in the two-buffer layout; NULL = the current state, in either scheme),
+ * u with the +F/2 shift; per-cell values in
  * FP32, summed in FP64.  out: host, 1 double.  Synchronises `stream`.
  * Errors: LBM_EINVAL, LBM_ESTATE, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE. */
 lbm_status lbm_kinetic_energy(lbm_ctx *ctx, const void *f, double *out, void *stream);

@@ -27,6 +27,7 @@ struct lbm_ctx {
     const float *Ffield;
     bool bound;
     bool state_set;
+    bool inplace;  // single-buffer (AA) streaming; g.layout tracks the state's layout
     int device;
     double *red_scratch;  // partial sums + 4 totals
     int red_blocks;
@@ -113,6 +114,12 @@ struct StepFn {
     }
 };
 template <int Q, typename T>
+struct StepAAFn {
+    static cudaError_t run(void *buf, const lbm::StepArgs &a, bool even, cudaStream_t s) {
+        return lbm::launch_step_aa<Q, T>(buf, a, even, s);
+    }
+};
+template <int Q, typename T>
 struct InitFn {
     static cudaError_t run(void *buf, const lbm::StepArgs &a, const double *rho, const double *u,
                            cudaStream_t s) {
@@ -159,7 +166,9 @@ lbm_status lbm_create(lbm_lattice lattice, int nx, int ny, int nz, const double 
     if (Q != 27 && Q != 15) return LBM_EINVAL;
     if (nx < 1 || ny < 1 || nz < 1) return LBM_EINVAL;
     if (ny > 65535 || nz > 65535) return LBM_EINVAL;  // launch grid limits (y, z)
-    if (bc_flags & ~(LBM_WALL_Y | LBM_WALL_Z)) return LBM_EINVAL;
+    if (bc_flags & ~(LBM_WALL_Y | LBM_WALL_Z | LBM_INPLACE)) return LBM_EINVAL;
+    const bool inplace = (bc_flags & LBM_INPLACE) != 0;
+    if (inplace && (nx % 2) != 0) return LBM_EINVAL;  // the in-place kernels take cell pairs
     if (storage != LBM_STORE_F32 && storage != LBM_STORE_F16 && storage != LBM_STORE_BF16)
         return LBM_EINVAL;
     if (!valid_rates(Q, omega)) return LBM_EINVAL;
@@ -180,7 +189,9 @@ lbm_status lbm_create(lbm_lattice lattice, int nx, int ny, int nz, const double 
     c->g.ny = ny;
     c->g.nz = nz;
     c->g.px = int(px);
-    c->g.bc = bc_flags;
+    c->g.bc = bc_flags & (LBM_WALL_Y | LBM_WALL_Z);
+    c->g.layout = inplace ? lbm::kAANatural : lbm::kPull;
+    c->inplace = inplace;
     c->g.plane = px * ny;
     c->g.pop = px * ny * nz;
     for (int b = 0; b < 27; ++b) c->w[b] = (b >= 4 && b < Q) ? float(omega[b]) : 0.0f;
@@ -206,6 +217,18 @@ size_t lbm_state_bytes(const lbm_ctx *c) {
 int lbm_row_pitch(const lbm_ctx *c) { return c ? c->g.px : 0; }
 
 lbm_status lbm_bind(lbm_ctx *c, void *f_a, void *f_b, const float *force_field) {
+    if (c && c->inplace) {
+        if (!f_a || f_b || (reinterpret_cast<uintptr_t>(f_a) & 255u)) return LBM_EINVAL;
+        if (force_field && (reinterpret_cast<uintptr_t>(force_field) & 3u)) return LBM_EINVAL;
+        c->buf[0] = f_a;
+        c->buf[1] = nullptr;
+        c->cur = 0;
+        c->g.layout = lbm::kAANatural;
+        c->Ffield = force_field;
+        c->bound = true;
+        c->state_set = false;
+        return LBM_OK;
+    }
     if (!c || !f_a || !f_b || f_a == f_b) return LBM_EINVAL;
     if ((reinterpret_cast<uintptr_t>(f_a) | reinterpret_cast<uintptr_t>(f_b)) & 255u)
         return LBM_EINVAL;
@@ -247,6 +270,7 @@ lbm_status lbm_set_omega(lbm_ctx *c, const double *omega) {
 lbm_status lbm_init_equilibrium(lbm_ctx *c, const double *rho, const double *u, void *stream) {
     if (!c || !rho || !u) return LBM_EINVAL;
     if (!c->bound) return LBM_ESTATE;
+    if (c->inplace) c->g.layout = lbm::kAANatural;
     const lbm::StepArgs a = step_args(c);
     cudaError_t e = dispatch<InitFn>(c, c->buf[c->cur], a, rho, u, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
@@ -257,6 +281,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx *c, const double *rho, const double *u, 
 lbm_status lbm_set_state(lbm_ctx *c, const double *f, void *stream) {
     if (!c || !f) return LBM_EINVAL;
     if (!c->bound) return LBM_ESTATE;
+    if (c->inplace) c->g.layout = lbm::kAANatural;
     cudaError_t e = dispatch<SetFn>(c, c->buf[c->cur], c->g, f, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->state_set = true;
@@ -275,6 +300,16 @@ lbm_status lbm_get_state(const lbm_ctx *c, double *f, void *stream) {
 lbm_status lbm_step(lbm_ctx *c, int nsteps, void *stream) {
     if (!c || nsteps < 0) return LBM_EINVAL;
     if (!c->bound || !c->state_set) return LBM_ESTATE;
+    if (c->inplace) {
+        for (int s = 0; s < nsteps; ++s) {
+            const lbm::StepArgs a = step_args(c);
+            const bool even = c->g.layout == lbm::kAANatural;
+            cudaError_t e = dispatch<StepAAFn>(c, c->buf[0], a, even, (cudaStream_t)stream);
+            if (e != cudaSuccess) return cuda_fail(c, e);
+            c->g.layout = even ? lbm::kAASwapped : lbm::kAANatural;
+        }
+        return LBM_OK;
+    }
     const lbm::StepArgs a = step_args(c);
     for (int s = 0; s < nsteps; ++s) {
         cudaError_t e = dispatch<StepFn>(c, (const void *)c->buf[c->cur], c->buf[1 - c->cur], a,
@@ -344,7 +379,7 @@ size_t lbm_adjoint_bytes(const lbm_ctx *c) {
 }
 
 const void *lbm_current_state(const lbm_ctx *c) {
-    if (!c || !c->bound || !c->state_set) return nullptr;
+    if (!c || !c->bound || !c->state_set || c->inplace) return nullptr;
     return c->buf[c->cur];
 }
 
@@ -358,6 +393,7 @@ lbm_status lbm_step_into(lbm_ctx *c, const void *f_in, void *f_out, void *stream
     const size_t bytes = lbm_state_bytes(c);
     const char *a = static_cast<const char *>(f_in), *b = static_cast<const char *>(f_out);
     if (a < b + bytes && b < a + bytes) return LBM_EINVAL;
+    if (c->inplace) return LBM_EUNSUPPORTED;
     const lbm::StepArgs args = step_args(c);
     cudaError_t e = dispatch<StepFn>(c, f_in, f_out, args, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
@@ -371,7 +407,7 @@ lbm_status lbm_adjoint_step(lbm_ctx *c, const void *f_t, const float *lam_next, 
     if ((reinterpret_cast<uintptr_t>(lam_next) | reinterpret_cast<uintptr_t>(lam_out)) & 15u)
         return LBM_EINVAL;
     if (dJdF && (reinterpret_cast<uintptr_t>(dJdF) & 3u)) return LBM_EINVAL;
-    if (c->Q != 27) return LBM_EUNSUPPORTED;
+    if (c->Q != 27 || c->inplace) return LBM_EUNSUPPORTED;
     const lbm::StepArgs a = step_args(c);
     cudaError_t e = dispatch_storage<AdjointFn>(c, f_t, lam_next, lam_out, dJdF, a,
                                                 (cudaStream_t)stream);
@@ -382,13 +418,15 @@ lbm_status lbm_adjoint_step(lbm_ctx *c, const void *f_t, const float *lam_next, 
 lbm_status lbm_kinetic_energy_seed(lbm_ctx *c, const void *f, float *lam_out, float *dJdF,
                                    void *stream) {
     if (!c || !lam_out) return LBM_EINVAL;
+    lbm::StepArgs a = step_args(c);
     if (!f) {
         if (!c->bound || !c->state_set) return LBM_ESTATE;
         f = c->buf[c->cur];
+    } else {
+        a.g.layout = lbm::kPull;  // a caller's buffer holds a two-buffer state
     }
     if (!state_buffer_ok(f) || (reinterpret_cast<uintptr_t>(lam_out) & 15u)) return LBM_EINVAL;
     if (c->Q != 27) return LBM_EUNSUPPORTED;
-    const lbm::StepArgs a = step_args(c);
     cudaError_t e = dispatch_storage<SeedFn>(c, f, lam_out, dJdF, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     return LBM_OK;
@@ -396,15 +434,17 @@ lbm_status lbm_kinetic_energy_seed(lbm_ctx *c, const void *f, float *lam_out, fl
 
 lbm_status lbm_kinetic_energy(lbm_ctx *c, const void *f, double *out, void *stream) {
     if (!c || !out) return LBM_EINVAL;
+    lbm::StepArgs a = step_args(c);
     if (!f) {
         if (!c->bound || !c->state_set) return LBM_ESTATE;
         f = c->buf[c->cur];
+    } else {
+        a.g.layout = lbm::kPull;  // a caller's buffer holds a two-buffer state
     }
     if (!state_buffer_ok(f)) return LBM_EINVAL;
     const int blocks = lbm::conservation_blocks(c->g);
     const lbm_status ms = ensure_scratch(c, blocks);
     if (ms != LBM_OK) return ms;
-    const lbm::StepArgs a = step_args(c);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = dispatch<EnergyFn>(c, f, a, c->red_scratch, blocks, s);
     if (e != cudaSuccess) return cuda_fail(c, e);

@@ -148,6 +148,7 @@ struct Pair<float> {
     __device__ __forceinline__ static void st2(float *p, f2 v) {
         __stcs(reinterpret_cast<float2 *>(p), make_float2(v.lo(), v.hi()));
     }
+    __device__ __forceinline__ static void st1(float *p, float v) { __stcs(p, v); }
 };
 template <>
 struct Pair<__half> {
@@ -162,6 +163,7 @@ struct Pair<__half> {
         const __half2 h = __floats2half2_rn(v.lo(), v.hi());
         __stcs(reinterpret_cast<unsigned int *>(p), *reinterpret_cast<const unsigned int *>(&h));
     }
+    __device__ __forceinline__ static void st1(__half *p, float v) { Storage<__half>::store(p, v); }
 };
 template <>
 struct Pair<__nv_bfloat16> {
@@ -175,6 +177,9 @@ struct Pair<__nv_bfloat16> {
     __device__ __forceinline__ static void st2(__nv_bfloat16 *p, f2 v) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(v.lo(), v.hi());
         __stcs(reinterpret_cast<unsigned int *>(p), *reinterpret_cast<const unsigned int *>(&h));
+    }
+    __device__ __forceinline__ static void st1(__nv_bfloat16 *p, float v) {
+        Storage<__nv_bfloat16>::store(p, v);
     }
 };
 
@@ -360,6 +365,134 @@ __global__ void __launch_bounds__(128) step2_q15_kernel(const StepIO<T> io, cons
         constexpr int q = decltype(iq)::value;
         const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<15>(q))) : f[q];
         Pair<T>::st2(io.out[q] + R.own + x0, v);
+    });
+}
+
+// ---- in-place (AA) streaming: one buffer, two kinds of step -------------
+//
+// Even step (layout kAANatural -> kAASwapped): each cell reads its own
+// populations f_a(x) from slot a, collides, and writes f~_a(x) back to its
+// own cell, slot opp(a).  Odd step (kAASwapped -> kAANatural): each cell
+// reads f_a(x) = f~_a(x - e_a) from slot opp(a) of its upstream neighbour (or
+// from its own slot a behind a bounce-back wall), collides, and writes
+// f~_a(x) to slot a of its downstream neighbour x + e_a (or to its own slot
+// opp(a) when x + e_a is behind a wall), where the next even step reads it.
+// In both steps a thread reads and writes the same set of locations, so the
+// update is race-free in place.  Both use two cells per thread (nx even).
+
+template <int Q>
+struct PairCollide;
+template <>
+struct PairCollide<27> {
+    __device__ __forceinline__ static void run(f2 (&f)[27], f2 Fx, f2 Fy, f2 Fz,
+                                               const PackedRates &pr, bool) {
+        const Rates27<f2> r = load_rates_packed(pr);
+        collide27<f2>(f, Fx, Fy, Fz, r);
+    }
+};
+template <>
+struct PairCollide<15> {
+    __device__ __forceinline__ static void run(f2 (&f)[15], f2 Fx, f2 Fy, f2 Fz,
+                                               const PackedRates &pr, bool has_force) {
+        Rates15<f2> r;
+#pragma unroll
+        for (int b = 0; b < 15; ++b) r.w[b] = f2(pr.w15[b]);
+        collide15<f2>(f, Fx, Fy, Fz, r, has_force);
+    }
+};
+
+__device__ __forceinline__ void pair_force(const StepArgs &a, int x0, int y, int z, f2 &Fx, f2 &Fy,
+                                           f2 &Fz) {
+    if (a.Ffield) {
+        const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
+        const long long c = dense_index(a.g, x0, y, z);
+        Fx = f2(__ldg(a.Ffield + c), __ldg(a.Ffield + c + 1));
+        Fy = f2(__ldg(a.Ffield + N + c), __ldg(a.Ffield + N + c + 1));
+        Fz = f2(__ldg(a.Ffield + 2 * N + c), __ldg(a.Ffield + 2 * N + c + 1));
+    } else {
+        Fx = f2(a.F[0]);
+        Fy = f2(a.F[1]);
+        Fz = f2(a.F[2]);
+    }
+}
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const StepArgs a,
+                                                      const PackedRates pr) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    const int x0 = 2 * t;
+    if (x0 >= a.g.nx || y >= a.g.ny) return;
+    const int own = (z * a.g.ny + y) * a.g.px + x0;
+    f2 f[Q];
+    static_for<Q>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        const f2 v = Pair<T>::ld2(io.in[q] + own);
+        f[q] = Storage<T>::kScaled ? v * f2(float(weight<Q>(q))) : v;
+    });
+    f2 Fx, Fy, Fz;
+    pair_force(a, x0, y, z, Fx, Fy, Fz);
+    PairCollide<Q>::run(f, Fx, Fy, Fz, pr, a.has_force != 0);
+    static_for<Q>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<Q>(q))) : f[q];
+        Pair<T>::st2(io.out[opposite<Q>(q)] + own, v);
+    });
+}
+
+template <int Q, typename T, bool kWalls>
+__global__ void __launch_bounds__(128) aa_odd_kernel(const StepIO<T> io, const StepArgs a,
+                                                     const PackedRates pr) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    const int x0 = 2 * t;
+    if (x0 >= a.g.nx || y >= a.g.ny) return;
+    const Rows<kWalls> R = pull_rows<kWalls>(a.g, y, z);
+    const int xm = (x0 == 0) ? a.g.nx - 1 : x0 - 1;
+    const int xp = (x0 + 2 == a.g.nx) ? 0 : x0 + 2;
+    const int own = R.own + x0;
+    f2 f[Q];
+    static_for<Q>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        constexpr int i = ex<Q>(q), j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
+        constexpr int o = opposite<Q>(q);
+        f2 v;
+        if (kWalls && R.wall[j][k]) {
+            v = Pair<T>::ld2(io.in[q] + own);
+        } else {
+            const T *row = io.in[o] + R.off[j][k];
+            if constexpr (i == 0)
+                v = Pair<T>::ld2(row + x0);
+            else if constexpr (i == 1)
+                v = f2(Pair<T>::ld1(row + xm), Pair<T>::ld1(row + x0));
+            else
+                v = f2(Pair<T>::ld1(row + x0 + 1), Pair<T>::ld1(row + xp));
+        }
+        f[q] = Storage<T>::kScaled ? v * f2(float(weight<Q>(q))) : v;
+    });
+    f2 Fx, Fy, Fz;
+    pair_force(a, x0, y, z, Fx, Fy, Fz);
+    PairCollide<Q>::run(f, Fx, Fy, Fz, pr, a.has_force != 0);
+    static_for<Q>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        constexpr int i = ex<Q>(q), j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
+        constexpr int o = opposite<Q>(q);
+        const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<Q>(q))) : f[q];
+        // downstream neighbour x + e_q: the row of the mirrored pull
+        if (kWalls && R.wall[2 - j][2 - k]) {
+            Pair<T>::st2(io.out[o] + own, v);
+        } else {
+            T *row = io.out[q] + R.off[2 - j][2 - k];
+            if constexpr (i == 0) {
+                Pair<T>::st2(row + x0, v);
+            } else if constexpr (i == 1) {
+                Pair<T>::st1(row + x0 + 1, v.lo());
+                Pair<T>::st1(row + xp, v.hi());
+            } else {
+                Pair<T>::st1(row + xm, v.lo());
+                Pair<T>::st1(row + x0, v.hi());
+            }
+        }
     });
 }
 
@@ -557,6 +690,28 @@ cudaError_t launch_step(const void *fin, void *fout, const StepArgs &a, cudaStre
     return cudaGetLastError();
 }
 
+// One in-place (AA) step on buffer buf: even (kAANatural -> kAASwapped) or
+// odd (kAASwapped -> kAANatural).  nx must be even.
+template <int Q, typename T>
+cudaError_t launch_step_aa(void *buf, const StepArgs &a, bool even, cudaStream_t st) {
+    StepIO<T> io;
+    for (int q = 0; q < 27; ++q) {
+        io.in[q] = static_cast<const T *>(buf) + (q < Q ? q * a.g.pop : 0);
+        io.out[q] = static_cast<T *>(buf) + (q < Q ? q * a.g.pop : 0);
+    }
+    Grid half = a.g;
+    half.nx = a.g.nx / 2;
+    const CellLaunch L = cell_launch(half);
+    const PackedRates pr = packed_rates(a);
+    if (even)
+        aa_even_kernel<Q, T><<<L.grid, L.block, 0, st>>>(io, a, pr);
+    else if (a.g.bc)
+        aa_odd_kernel<Q, T, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+    else
+        aa_odd_kernel<Q, T, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
+    return cudaGetLastError();
+}
+
 template <int Q, typename T>
 cudaError_t launch_init(void *buf, const StepArgs &a, const double *rho, const double *u,
                         cudaStream_t st) {
@@ -610,6 +765,7 @@ inline int conservation_blocks(const Grid &g) {
 #define LBM_INSTANTIATE_1(EXT, Q, T)                                                             \
     EXT template cudaError_t launch_step<Q, T>(const void *, void *, const StepArgs &,          \
                                                cudaStream_t);                                  \
+    EXT template cudaError_t launch_step_aa<Q, T>(void *, const StepArgs &, bool, cudaStream_t);  \
     EXT template cudaError_t launch_init<Q, T>(void *, const StepArgs &, const double *,         \
                                                const double *, cudaStream_t);                  \
     EXT template cudaError_t launch_set_state<Q, T>(void *, const Grid &, const double *,        \

@@ -148,12 +148,26 @@ __device__ __forceinline__ void store_dev(T *p, int a, float dev) {
 }
 
 // ---------------------------------------------------------------------- grid
+// How a state buffer holds the pre-collision distributions f(x, t):
+//   kPull:      post-collision values of the previous step at their own cells
+//               (two-buffer pull scheme): f_a(x) = buf[a](x - e_a), or
+//               buf[opp a](x) behind a bounce-back wall;
+//   kAANatural: single-buffer (AA) scheme, a freshly loaded state or one
+//               after an even number of in-place steps: f_a(x) = buf[a](x);
+//   kAASwapped: AA scheme after an odd number of in-place steps (the last
+//               one collided in place without streaming):
+//               f_a(x) = buf[opp a](x - e_a), or buf[a](x) behind a wall.
+constexpr int kPull = 0;
+constexpr int kAANatural = 1;
+constexpr int kAASwapped = 2;
+
 struct Grid {
     int nx, ny, nz;   // cells
     int px;           // row pitch in elements
     unsigned bc;      // kWallY | kWallZ
     long long plane;  // px * ny
     long long pop;    // px * ny * nz: distance between populations
+    int layout;       // kPull, kAANatural or kAASwapped (state reads and writes)
 };
 
 // Source coordinates of the pull for one cell.  Index 0, 1, 2 of each array
@@ -204,19 +218,18 @@ __device__ __forceinline__ void gather(const T *__restrict__ fin, const Grid &g,
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int j = ey<Q>(a) + 1, k = ez<Q>(a) + 1, i = ex<Q>(a) + 1;
+        const int o = opposite<Q>(a);
         long long idx;
-        int slot;
-        if (s.wall[j][k]) {
-            slot = opposite<Q>(a);
-            idx = (long long)slot * g.pop + s.own;
+        if (g.layout == kAANatural) {
+            idx = (long long)a * g.pop + s.own;
+        } else if (s.wall[j][k]) {
+            idx = (long long)(g.layout == kPull ? o : a) * g.pop + s.own;
         } else {
-            slot = a;
-            idx = (long long)a * g.pop + s.row[j][k] + s.xs[i];
+            idx = (long long)(g.layout == kPull ? a : o) * g.pop + s.row[j][k] + s.xs[i];
         }
         const float v = Storage<T>::load(fin + idx);
         // the weight of a slot and of its opposite are equal
         f[a] = Storage<T>::kScaled ? v * float(weight<Q>(a)) : v;
-        (void)slot;
     }
 }
 
@@ -229,10 +242,16 @@ __device__ __forceinline__ void store_own(T *__restrict__ fout, const Grid &g, l
 }
 
 // Inverse of the pull: place the pre-collision values f_alpha(x) of one cell
-// where the next pull will read them (used to load a state).
+// where the next step will read them (used to load a state; the AA scheme
+// loads into its natural layout).
 template <int Q, typename T>
 __device__ __forceinline__ void scatter_state(T *__restrict__ buf, const Grid &g,
                                               const PullSources &s, const float (&f)[Q]) {
+    if (g.layout != kPull) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) store_dev<Q, T>(buf + (long long)a * g.pop + s.own, a, f[a]);
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int j = ey<Q>(a) + 1, k = ez<Q>(a) + 1, i = ex<Q>(a) + 1;

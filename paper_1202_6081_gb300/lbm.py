@@ -27,6 +27,7 @@ LBM_STORE_F16 = 1
 LBM_STORE_BF16 = 2
 LBM_WALL_Y = 1
 LBM_WALL_Z = 2
+LBM_INPLACE = 4
 STORAGE = {"f32": LBM_STORE_F32, "f16": LBM_STORE_F16, "bf16": LBM_STORE_BF16}
 
 LBM_OK = 0
@@ -249,10 +250,11 @@ class Solver:
     shape = (nz, ny, nx); omega: Q relaxation rates (0..3 ignored); force:
     uniform F (3,) or a per-cell field [3, nz, ny, nx] (device FP32 tensor or
     array); walls: OR of LBM_WALL_Y / LBM_WALL_Z; storage: "f32", "f16" or
-    "bf16"."""
+    "bf16"; inplace: one state buffer with in-place (AA) streaming (nx
+    even; no step_into / adjoint)."""
 
     def __init__(self, Q, shape, omega, force=(0.0, 0.0, 0.0), walls=0, storage="f32",
-                 device=None):
+                 device=None, inplace=False):
         self.Q = int(Q)
         self.shape = tuple(int(s) for s in shape)
         nz, ny, nx = self.shape
@@ -260,6 +262,7 @@ class Solver:
             "cuda", torch.cuda.current_device())
         self.storage = storage
         self.walls = walls
+        self.inplace = bool(inplace)
         self.omega = np.asarray(omega, dtype=np.float64)
         with torch.cuda.device(self.device):
             field = None
@@ -271,11 +274,13 @@ class Solver:
                 field = torch.as_tensor(F, dtype=torch.float32).reshape(3, nz, ny, nx)
                 field = field.to(self.device).contiguous()
             self.force_field = field
-            self.ctx = lbm_create(self.Q, nx, ny, nz, self.omega, uniform, walls, STORAGE[storage])
+            flags = walls | (LBM_INPLACE if self.inplace else 0)
+            self.ctx = lbm_create(self.Q, nx, ny, nz, self.omega, uniform, flags, STORAGE[storage])
             nbytes = lbm_state_bytes(self.ctx)
             self.buffers = [torch.empty(nbytes, dtype=torch.uint8, device=self.device)
-                            for _ in range(2)]
-            lbm_bind(self.ctx, self.buffers[0], self.buffers[1], field)
+                            for _ in range(1 if self.inplace else 2)]
+            lbm_bind(self.ctx, self.buffers[0], self.buffers[1] if len(self.buffers) > 1 else None,
+                     field)
 
     def __del__(self):
         ctx = getattr(self, "ctx", None)
