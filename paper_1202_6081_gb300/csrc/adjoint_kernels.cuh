@@ -62,6 +62,70 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const StepIO<T> io, const 
     }
 }
 
+// The same adjoint step for two neighbouring cells (x0, x0 + 1) per thread in
+// packed f32x2 arithmetic (nx even).  The state is pulled as in step2_kernel;
+// the adjoint is pulled from the mirrored neighbours x + e_q: for e_x = 0 an
+// aligned pair, for e_x = +1 the cells (x0 + 1, x0 + 2), for e_x = -1
+// (x0 - 1, x0).
+template <typename T, bool kWalls>
+__global__ void __launch_bounds__(128, 3) adjoint2_kernel(const StepIO<T> io, const AdjointArgs g,
+                                                       const StepArgs a, const PackedRates pr) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    const int x0 = 2 * t;
+    if (x0 >= a.g.nx || y >= a.g.ny) return;
+    const Rows<kWalls> R = pull_rows<kWalls>(a.g, y, z);
+    const int xm = (x0 == 0) ? a.g.nx - 1 : x0 - 1;
+    const int xp = (x0 + 2 == a.g.nx) ? 0 : x0 + 2;
+    const int own = R.own + x0;
+    f2 f[27], mu[27];
+    static_for<27>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        constexpr int i = ex<27>(q), j = ey<27>(q) + 1, k = ez<27>(q) + 1;
+        constexpr int o = opposite<27>(q);
+        const f2 v = pull_pair<27, T, kWalls>(io, R, q, x0, xm, xp);
+        f[q] = Storage<T>::kScaled ? v * f2(float(weight<27>(q))) : v;
+        if (kWalls && R.wall[2 - j][2 - k]) {
+            mu[q] = Pair<float>::ld2(g.lam_next[o] + own);
+        } else {
+            const float *row = g.lam_next[q] + R.off[2 - j][2 - k];
+            if constexpr (i == 0)
+                mu[q] = Pair<float>::ld2(row + x0);
+            else if constexpr (i == 1)
+                mu[q] = f2(__ldg(row + x0 + 1), __ldg(row + xp));
+            else
+                mu[q] = f2(__ldg(row + xm), __ldg(row + x0));
+        }
+    });
+    const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
+    const long long c = dense_index(a.g, x0, y, z);
+    f2 Fx, Fy, Fz;
+    if (a.Ffield) {  // 4-byte alignment only is required of the field: single loads
+        Fx = f2(__ldg(a.Ffield + c), __ldg(a.Ffield + c + 1));
+        Fy = f2(__ldg(a.Ffield + N + c), __ldg(a.Ffield + N + c + 1));
+        Fz = f2(__ldg(a.Ffield + 2 * N + c), __ldg(a.Ffield + 2 * N + c + 1));
+    } else {
+        Fx = f2(a.F[0]);
+        Fy = f2(a.F[1]);
+        Fz = f2(a.F[2]);
+    }
+    const Rates27<f2> r = load_rates_packed(pr);
+    f2 lam[27], gx, gy, gz;
+    adjoint27<f2>(f, Fx, Fy, Fz, r, mu, lam, gx, gy, gz);
+    static_for<27>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        Pair<float>::st2(g.lam_out[q] + own, lam[q]);
+    });
+    if (g.gF) {
+        g.gF[c] += gx.lo();
+        g.gF[c + 1] += gx.hi();
+        g.gF[N + c] += gy.lo();
+        g.gF[N + c + 1] += gy.hi();
+        g.gF[2 * N + c] += gz.lo();
+        g.gF[2 * N + c + 1] += gz.hi();
+    }
+}
+
 // Seed of the adjoint for J = sum_x rho |u|^2 / 2 at the final state:
 // lam_a = u.e_a - |u|^2 / 2, and the direct term dJ/dF += u / 2
 // (u = (j + F/2) / rho).
@@ -139,6 +203,17 @@ cudaError_t launch_adjoint(const void *f_t, const float *lam_next, float *lam_ou
         g.lam_out[q] = lam_out + q * a.g.pop;
     }
     g.gF = gF;
+    if (a.g.nx % 2 == 0) {
+        Grid half = a.g;
+        half.nx = a.g.nx / 2;
+        const CellLaunch L = cell_launch(half);
+        const PackedRates pr = packed_rates(a);
+        if (a.g.bc)
+            adjoint2_kernel<T, true><<<L.grid, L.block, 0, st>>>(io, g, a, pr);
+        else
+            adjoint2_kernel<T, false><<<L.grid, L.block, 0, st>>>(io, g, a, pr);
+        return cudaGetLastError();
+    }
     const CellLaunch L = cell_launch(a.g);
     if (a.g.bc)
         adjoint_kernel<T, true><<<L.grid, L.block, 0, st>>>(io, g, a);

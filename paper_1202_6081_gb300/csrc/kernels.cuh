@@ -148,10 +148,34 @@ struct Pair<float> {
     __device__ __forceinline__ static void st2(float *p, f2 v) {
         __stcs(reinterpret_cast<float2 *>(p), make_float2(v.lo(), v.hi()));
     }
-    __device__ __forceinline__ static void st1(float *p, float v) { __stcs(p, v); }
+    // the step's stores (plain stores for FP32; see Pair16 for 16-bit)
+    template <int q>
+    __device__ __forceinline__ static void st2s(float *p, f2 v, unsigned) {
+        st2(p, v);
+    }
+    template <int q>
+    __device__ __forceinline__ static void st1x2s(float *plo, float *phi, f2 v, unsigned) {
+        __stcs(plo, v.lo());
+        __stcs(phi, v.hi());
+    }
+};
+// 16-bit step stores: the pair is rounded together (pack_sr) and stored as one
+// 32-bit word, or as two halves at separate addresses.
+template <typename T>
+struct Pair16 {
+    template <int q>
+    __device__ __forceinline__ static void st2s(T *p, f2 v, unsigned salt) {
+        __stcs(reinterpret_cast<unsigned int *>(p), pack_sr<T, q>(v.lo(), v.hi(), salt));
+    }
+    template <int q>
+    __device__ __forceinline__ static void st1x2s(T *plo, T *phi, f2 v, unsigned salt) {
+        const unsigned d = pack_sr<T, q>(v.lo(), v.hi(), salt);
+        __stcs(reinterpret_cast<unsigned short *>(plo), static_cast<unsigned short>(d & 0xffffu));
+        __stcs(reinterpret_cast<unsigned short *>(phi), static_cast<unsigned short>(d >> 16));
+    }
 };
 template <>
-struct Pair<__half> {
+struct Pair<__half> : Pair16<__half> {
     __device__ __forceinline__ static f2 ld2(const __half *p) {
         const float2 v = __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
         return f2(v.x, v.y);
@@ -159,27 +183,15 @@ struct Pair<__half> {
     __device__ __forceinline__ static float ld1(const __half *p) {
         return __half2float(__ldg(p));
     }
-    __device__ __forceinline__ static void st2(__half *p, f2 v) {
-        const __half2 h = __floats2half2_rn(v.lo(), v.hi());
-        __stcs(reinterpret_cast<unsigned int *>(p), *reinterpret_cast<const unsigned int *>(&h));
-    }
-    __device__ __forceinline__ static void st1(__half *p, float v) { Storage<__half>::store(p, v); }
 };
 template <>
-struct Pair<__nv_bfloat16> {
+struct Pair<__nv_bfloat16> : Pair16<__nv_bfloat16> {
     __device__ __forceinline__ static f2 ld2(const __nv_bfloat16 *p) {
         const float2 v = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
         return f2(v.x, v.y);
     }
     __device__ __forceinline__ static float ld1(const __nv_bfloat16 *p) {
         return __bfloat162float(__ldg(p));
-    }
-    __device__ __forceinline__ static void st2(__nv_bfloat16 *p, f2 v) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v.lo(), v.hi());
-        __stcs(reinterpret_cast<unsigned int *>(p), *reinterpret_cast<const unsigned int *>(&h));
-    }
-    __device__ __forceinline__ static void st1(__nv_bfloat16 *p, float v) {
-        Storage<__nv_bfloat16>::store(p, v);
     }
 };
 
@@ -257,8 +269,10 @@ __global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const Ste
     cell_force(a, dense_index(a.g, x, y, z), N, Fx, Fy, Fz);
     const typename Rates<Q>::type r = load_rates<Q>(a);
     collide<Q>(f, Fx, Fy, Fz, r, a.has_force != 0);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) store_dev<Q, T>(io.out[q] + R.own + x, q, f[q]);
+    static_for<Q>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        store_dev_step<Q, T, q>(io.out[q] + R.own + x, f[q], sr_salt(R.own + x));
+    });
 }
 
 // One fused D3Q27 step, two neighbouring cells (x0, x0 + 1) per thread with
@@ -307,11 +321,11 @@ __global__ void __launch_bounds__(128) step2_kernel(const StepIO<T> io, const St
     }
     const Rates27<f2> r = load_rates_packed(pr);
     collide27<f2>(f, Fx, Fy, Fz, r);
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
+    static_for<27>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
         const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<27>(q))) : f[q];
-        Pair<T>::st2(io.out[q] + R.own + x0, v);
-    }
+        Pair<T>::template st2s<q>(io.out[q] + R.own + x0, v, sr_salt(R.own + x0));
+    });
 }
 
 // Pair gather for lattice Q: population q of cells (x0, x0 + 1) from the pull
@@ -364,7 +378,7 @@ __global__ void __launch_bounds__(128) step2_q15_kernel(const StepIO<T> io, cons
     static_for<15>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
         const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<15>(q))) : f[q];
-        Pair<T>::st2(io.out[q] + R.own + x0, v);
+        Pair<T>::template st2s<q>(io.out[q] + R.own + x0, v, sr_salt(R.own + x0));
     });
 }
 
@@ -436,7 +450,7 @@ __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const 
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
         const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<Q>(q))) : f[q];
-        Pair<T>::st2(io.out[opposite<Q>(q)] + own, v);
+        Pair<T>::template st2s<q>(io.out[opposite<Q>(q)] + own, v, sr_salt(own));
     });
 }
 
@@ -479,19 +493,17 @@ __global__ void __launch_bounds__(128) aa_odd_kernel(const StepIO<T> io, const S
         constexpr int o = opposite<Q>(q);
         const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<Q>(q))) : f[q];
         // downstream neighbour x + e_q: the row of the mirrored pull
+        const unsigned salt = sr_salt(own);
         if (kWalls && R.wall[2 - j][2 - k]) {
-            Pair<T>::st2(io.out[o] + own, v);
+            Pair<T>::template st2s<q>(io.out[o] + own, v, salt);
         } else {
             T *row = io.out[q] + R.off[2 - j][2 - k];
-            if constexpr (i == 0) {
-                Pair<T>::st2(row + x0, v);
-            } else if constexpr (i == 1) {
-                Pair<T>::st1(row + x0 + 1, v.lo());
-                Pair<T>::st1(row + xp, v.hi());
-            } else {
-                Pair<T>::st1(row + xm, v.lo());
-                Pair<T>::st1(row + x0, v.hi());
-            }
+            if constexpr (i == 0)
+                Pair<T>::template st2s<q>(row + x0, v, salt);
+            else if constexpr (i == 1)
+                Pair<T>::template st1x2s<q>(row + x0 + 1, row + xp, v, salt);
+            else
+                Pair<T>::template st1x2s<q>(row + xm, row + x0, v, salt);
         }
     });
 }

@@ -131,6 +131,62 @@ struct Storage<__nv_bfloat16> {
     }
 };
 
+// ------------------------------------------------- stochastic 16-bit rounding
+// The step stores 16-bit values with stochastic rounding: up or down with
+// probability proportional to the distance, so each stored value is exact
+// in expectation.  Round-to-nearest of a smooth field gives a rounding error
+// that is itself a smooth function of position wherever the field is flat,
+// and that coherent error is re-made identically every step and accumulates
+// (FP16 storage of the 512^3 Taylor-Green flow drifts to 1.5e-3 relative
+// error of u in 500 steps that way).  The conversions are sm_100-class
+// cvt.rs.{f16x2,bf16x2}.f32, fed 32 random bits.  The bits are a hash of the
+// two values being rounded, of the cell pair's position and of the
+// population, so the rounding is a fixed function of the state: a step
+// recomputed from the same state (checkpointing) and the in-place scheme
+// round exactly as the two-buffer step does.
+
+// Salt of the cell (pair) at element offset own.
+__device__ __forceinline__ unsigned sr_salt(int own) { return static_cast<unsigned>(own); }
+
+// 32 random bits for population q from (lo, hi, salt): one multiply-xorshift
+// round on the XOR of the inputs (hi rotated by 16), with a distinct odd
+// multiplier per population.  Each lane's conversion reads 13 (FP16) or 16
+// (BF16) bits; the low lane's bits mix its own discarded bits with the other
+// lane's and the salt's through the product's high half, the high lane's
+// are its discarded bits plus a product of everything below them, so given
+// the bits being rounded away the random bits stay uniform.
+template <int q>
+__device__ __forceinline__ unsigned sr_bits(float lo, float hi, unsigned salt) {
+    constexpr unsigned kMul = 0x9E3779B1u + 2u * 0x2545F491u * static_cast<unsigned>(q);
+    const unsigned h = __float_as_uint(hi);
+    unsigned x = (__float_as_uint(lo) ^ __funnelshift_l(h, h, 16) ^ salt) * kMul;
+    return x ^ (x >> 16);
+}
+
+// (lo, hi) -> packed 16-bit pair (lo in the low half), stochastically rounded.
+template <typename T>
+struct PackSR;
+template <>
+struct PackSR<__half> {
+    __device__ __forceinline__ static unsigned run(float lo, float hi, unsigned bits) {
+        unsigned d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(bits));
+        return d;
+    }
+};
+template <>
+struct PackSR<__nv_bfloat16> {
+    __device__ __forceinline__ static unsigned run(float lo, float hi, unsigned bits) {
+        unsigned d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(bits));
+        return d;
+    }
+};
+template <typename T, int q>
+__device__ __forceinline__ unsigned pack_sr(float lo, float hi, unsigned salt) {
+    return PackSR<T>::run(lo, hi, sr_bits<q>(lo, hi, salt));
+}
+
 // Stored value -> deviation f - w (FP32), and back.
 template <int Q, typename T>
 __device__ __forceinline__ float load_dev(const T *p, int a) {
@@ -145,6 +201,18 @@ __device__ __forceinline__ void store_dev(T *p, int a, float dev) {
         Storage<T>::store(p, dev * float(1.0 / weight<Q>(a)));
     else
         Storage<T>::store(p, dev);
+}
+
+// The step's store of population a of one cell: FP32 as is, 16-bit
+// stochastically rounded.
+template <int Q, typename T, int a>
+__device__ __forceinline__ void store_dev_step(T *p, float dev, unsigned salt) {
+    if constexpr (Storage<T>::kScaled) {
+        const unsigned d = pack_sr<T, a>(dev * float(1.0 / weight<Q>(a)), 0.0f, salt);
+        __stcs(reinterpret_cast<unsigned short *>(p), static_cast<unsigned short>(d & 0xffffu));
+    } else {
+        Storage<T>::store(p, dev);
+    }
 }
 
 // ---------------------------------------------------------------------- grid

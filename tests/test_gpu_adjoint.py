@@ -45,9 +45,9 @@ def to_pitched(S, dense):
 
 @pytest.mark.parametrize("bc", [0, 3])
 @pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_adjoint_step_matches_oracle(lbm, orc, bc, storage):
+@pytest.mark.parametrize("shape", [(6, 7, 10), (6, 7, 9)])  # two-cell and one-cell kernels
+def test_adjoint_step_matches_oracle(lbm, orc, bc, storage, shape):
     Q = 27
-    shape = (6, 7, 10)
     rho, u = W.taylor_green(shape, u0=0.05, noise=1e-2, seed=31)
     om = W.random_omegas(Q, seed=32)
     F = f32(W.rng(33).uniform(-1e-3, 1e-3, (3,) + shape))

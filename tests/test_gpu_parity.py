@@ -214,11 +214,12 @@ def test_square_channel_steady_state_vs_series(lbm, Q):
     assert rel_l2(ux, ua) <= 1e-2
 
 
-@pytest.mark.parametrize("storage,bound", [("f16", 1e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("storage,bound", [("f16", 1e-3), ("bf16", 5e-3)])
 def test_16bit_storage_taylor_green(lbm, orc, storage, bound):
     """D3Q27 Taylor-Green + noise, 32^3, 100 steps, 16-bit storage of
-    (f - w)/w with FP32 arithmetic: velocity within the stated bound of the
-    FP64 oracle (FP16 meets 1e-3; BF16 is reported, not held to it)."""
+    (f - w)/w (stochastically rounded) with FP32 arithmetic: velocity within
+    the stated bound of the FP64 oracle (FP16 meets 1e-3; BF16, with an
+    8-bit significand, is reported and held to 5e-3)."""
     Q = 27
     shape = (32, 32, 32)
     om = W.omegas(Q, 1 / 0.6)
@@ -248,7 +249,7 @@ def tgv64_oracle(orc):
     return rho0, u0, u
 
 
-@pytest.mark.parametrize("storage,bound", [("f32", 1e-5), ("f16", 1e-3), ("bf16", 5e-2)])
+@pytest.mark.parametrize("storage,bound", [("f32", 1e-5), ("f16", 1e-3), ("bf16", 5e-3)])
 def test_storage_64cubed_500_steps_vs_oracle(lbm, orc, tgv64_oracle, storage, bound):
     """The 16-bit storage workload's flow and step count (Taylor-Green +
     noise, tau = 0.6, 500 steps) at 64^3, where the FP64 oracle finishes in
@@ -270,8 +271,9 @@ def test_16bit_storage_512cubed_500_steps_vs_fp32(lbm):
     """The 16-bit storage workload itself (512^3, Taylor-Green + noise,
     tau = 0.6, 500 steps): relative L2 of u of FP16 / BF16 storage against
     FP32 storage on the GPU (whose own error against the oracle is held to
-    1e-5 above).  FP16 round-to-nearest storage gives 1.5e-3 here, above the
-    1e-3 target it meets at 64^3 (2.3e-4): held to 2e-3 and reported."""
+    1e-5 above).  FP16 within 1e-3, BF16 reported and held to 5e-3.  (With
+    round-to-nearest stores instead of stochastic rounding the errors here
+    were 1.5e-3 and 1.5e-2, growing linearly with the step count.)"""
     Q = 27
     shape = (512, 512, 512)
     om = W.omegas(Q, 1 / 0.6)
@@ -290,8 +292,8 @@ def test_16bit_storage_512cubed_500_steps_vs_fp32(lbm):
     errs = {st: float((vel[st].double() - ref).norm() / ref.norm()) for st in ("f16", "bf16")}
     print("512^3 x 500 steps, rel L2 u vs FP32 storage: f16 %.3e, bf16 %.3e" % (
         errs["f16"], errs["bf16"]))
-    assert errs["f16"] <= 2e-3
-    assert errs["bf16"] <= 5e-2
+    assert errs["f16"] <= 1e-3
+    assert errs["bf16"] <= 5e-3
 
 
 def test_full_size_sampled_step_256(lbm, orc):
