@@ -226,6 +226,21 @@ lbm_status lbm_kinetic_energy(lbm_ctx *ctx, const void *f, double *out, void *st
 lbm_status lbm_kinetic_energy_seed(lbm_ctx *ctx, const void *f, float *lam_out, float *dJdF,
                                    void *stream);
 
+/* Seed of the adjoint of any objective J(rho, u) of the macroscopic fields
+ * of the state in f (a two-buffer state buffer; NULL = the current state),
+ * given its gradients g_rho = dJ/drho (device FP32 [nz][ny][nx]) and
+ * g_u = dJ/du (device FP32 [3][nz][ny][nx]); either may be NULL (zero).
+ * With rho and u of Eqs. densitycalculation and velocitycalculation
+ * (u = (sum f e + F/2) / rho), d rho/d f_a = 1 and d u_i/d f_a =
+ * (e_ai - u_i)/rho, so
+ *     lam_out_a(x) = g_rho(x) + sum_i (e_ai - u_i(x)) g_u_i(x) / rho(x),
+ * and, when dJdF is not NULL, the direct term dJdF_i += g_u_i / (2 rho).
+ * lam_out: an adjoint field (lbm_adjoint_bytes, 16-byte aligned).  Not in
+ * the paper (reverse mode of its output step).
+ * Errors: LBM_EINVAL, LBM_ESTATE, LBM_EUNSUPPORTED (D3Q15), LBM_ECUDA. */
+lbm_status lbm_macroscopic_seed(lbm_ctx *ctx, const void *f, const float *g_rho,
+                                const float *g_u, float *lam_out, float *dJdF, void *stream);
+
 /* Conservation sums for callers that cannot let the library allocate device
  * memory (the paper has no counterpart; this is a library service).  Same
  * sums as lbm_conservation, but asynchronous, into a caller buffer, and with

@@ -234,6 +234,20 @@ def kinetic_energy(Q: int, f, F):
     return float(0.5 * np.sum(rho * np.sum(u * u, axis=0)))
 
 
+def macroscopic_grad(Q: int, f, F, g_rho, g_u):
+    """Chain rule through Eqs. densitycalculation and velocitycalculation:
+    for J(rho, u) with dJ/drho = g_rho [...] and dJ/du = g_u [3, ...],
+    dJ/df_alpha = g_rho + sum_i (e_alpha,i - u_i) g_u_i / rho (rho = sum f,
+    rho u = sum f e + F/2) and the direct dJ/dF_i = g_u_i / (2 rho)."""
+    e, _, _, _ = lattice(Q)
+    rho, u = macroscopic(Q, f, F)
+    g_rho = np.broadcast_to(np.asarray(g_rho, dtype=np.float64), rho.shape)
+    g_u = np.asarray(g_u, dtype=np.float64)
+    dfl = np.stack([g_rho + sum((e[a, i] - u[i]) * g_u[i] for i in range(3)) / rho
+                    for a in range(Q)])
+    return dfl, g_u / (2.0 * rho)
+
+
 def kinetic_energy_grad(Q: int, f, F):
     """dJ/df [Q, ...] and the direct dJ/dF [3, ...] of ``kinetic_energy``:
     with j = sum f e + F/2, J = |j|^2 / (2 rho), so dJ/df_alpha =

@@ -2,6 +2,13 @@
 the library's discrete adjoint (not in the paper: the reverse mode of its
 update).
 
+``macroscopic_after(solver, F, nsteps, every, f0)`` returns the density and
+velocity fields (rho, u) after ``nsteps`` steps, differentiable with respect
+to the force field F and, when given, the initial state f0 (FP64
+[Q, nz, ny, nx]): any torch objective of (rho, u) can be back-propagated
+through the run.  Its backward seeds the adjoint with
+``lbm_macroscopic_seed`` from the incoming gradients of rho and u.
+
 ``kinetic_energy_after(solver, F, nsteps, every)`` returns
 J = sum_x rho |u|^2 / 2 after ``nsteps`` steps from the solver's current
 state under the force field F (device FP32 [3, nz, ny, nx]), as a
@@ -21,47 +28,103 @@ import torch
 class _KineticEnergyAfter(torch.autograd.Function):
     @staticmethod
     def forward(ctx, F, solver, nsteps, every):
-        if not (F.is_cuda and F.dtype == torch.float32 and F.is_contiguous()):
-            raise ValueError("F must be a contiguous CUDA float32 tensor [3, nz, ny, nx]")
+        _check_force(F)
         if nsteps < 1 or every < 1:
             raise ValueError("nsteps and every must be >= 1")
         solver.set_force_field(F)
-        ckpts = [solver.current_buffer().clone()]
-        for t in range(nsteps):
-            solver.step(1)
-            if (t + 1) % every == 0 and t + 1 < nsteps:
-                ckpts.append(solver.current_buffer().clone())
+        ckpts = _forward_with_checkpoints(solver, nsteps, every)
         J = solver.kinetic_energy()
-        ctx.solver = solver
-        ctx.nsteps = nsteps
-        ctx.every = every
-        ctx.ckpts = ckpts
+        ctx.solver, ctx.nsteps, ctx.every, ctx.ckpts = solver, nsteps, every, ckpts
         ctx.save_for_backward(F)
         return torch.tensor(J, dtype=torch.float64, device=F.device)
 
     @staticmethod
     def backward(ctx, gJ):
         (F,) = ctx.saved_tensors
-        S, nsteps, every, ckpts = ctx.solver, ctx.nsteps, ctx.every, ctx.ckpts
+        S = ctx.solver
         S.set_force_field(F)
         gF = torch.zeros_like(F)
-        lam = S.new_adjoint_field()
-        lam2 = S.new_adjoint_field()
-        ring = [S.new_state_buffer() for _ in range(min(every, nsteps) + 1)]
-        nseg = len(ckpts)
-        for s in reversed(range(nseg)):
-            t0 = s * every
-            t1 = min(t0 + every, nsteps)
-            ring[0].copy_(ckpts[s])
-            for i in range(t1 - t0):
-                S.step_into(ring[i], ring[i + 1])
-            if s == nseg - 1:
-                S.kinetic_energy_seed(ring[t1 - t0], lam, gF)
-            for i in reversed(range(t1 - t0)):
-                S.adjoint_step(ring[i], lam, lam2, gF)
-                lam, lam2 = lam2, lam
+
+        def seed(buf, lam):
+            S.kinetic_energy_seed(buf, lam, gF)
+
+        _backward_segments(S, ctx.nsteps, ctx.every, ctx.ckpts, seed, gF)
         ctx.ckpts = None
         return gF * gJ.to(gF.dtype), None, None, None
+
+
+def _check_force(F):
+    if not (F.is_cuda and F.dtype == torch.float32 and F.is_contiguous()):
+        raise ValueError("F must be a contiguous CUDA float32 tensor [3, nz, ny, nx]")
+
+
+def _forward_with_checkpoints(solver, nsteps, every):
+    ckpts = [solver.current_buffer().clone()]
+    for t in range(nsteps):
+        solver.step(1)
+        if (t + 1) % every == 0 and t + 1 < nsteps:
+            ckpts.append(solver.current_buffer().clone())
+    return ckpts
+
+
+def _backward_segments(S, nsteps, every, ckpts, seed, gF):
+    """Adjoint sweep over the checkpointed segments, last to first; `seed`
+    fills the adjoint field from the final state.  Returns the adjoint of
+    the initial state (a pitched FP32 field)."""
+    lam = S.new_adjoint_field()
+    lam2 = S.new_adjoint_field()
+    ring = [S.new_state_buffer() for _ in range(min(every, nsteps) + 1)]
+    nseg = len(ckpts)
+    for s in reversed(range(nseg)):
+        t0 = s * every
+        t1 = min(t0 + every, nsteps)
+        ring[0].copy_(ckpts[s])
+        for i in range(t1 - t0):
+            S.step_into(ring[i], ring[i + 1])
+        if s == nseg - 1:
+            seed(ring[t1 - t0], lam)
+        for i in reversed(range(t1 - t0)):
+            S.adjoint_step(ring[i], lam, lam2, gF)
+            lam, lam2 = lam2, lam
+    return lam
+
+
+class _MacroscopicAfter(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, F, f0, solver, nsteps, every):
+        _check_force(F)
+        if nsteps < 1 or every < 1:
+            raise ValueError("nsteps and every must be >= 1")
+        solver.set_force_field(F)
+        if f0 is not None:
+            solver.set_state(f0)
+        ckpts = _forward_with_checkpoints(solver, nsteps, every)
+        rho, u = solver.macroscopic()
+        ctx.solver, ctx.nsteps, ctx.every, ctx.ckpts = solver, nsteps, every, ckpts
+        ctx.has_f0 = f0 is not None
+        ctx.save_for_backward(F)
+        return rho, u
+
+    @staticmethod
+    def backward(ctx, g_rho, g_u):
+        (F,) = ctx.saved_tensors
+        S = ctx.solver
+        S.set_force_field(F)
+        gF = torch.zeros_like(F)
+
+        def seed(buf, lam):
+            S.macroscopic_seed(buf, g_rho, g_u, lam, gF)
+
+        lam0 = _backward_segments(S, ctx.nsteps, ctx.every, ctx.ckpts, seed, gF)
+        ctx.ckpts = None
+        g_f0 = S.adjoint_view(lam0).double() if ctx.has_f0 else None
+        return gF, g_f0, None, None, None
+
+
+def macroscopic_after(solver, F, nsteps, every=20, f0=None):
+    """Differentiable (rho, u) after nsteps steps under the force field F
+    (from the initial state f0 if given, else the solver's current state)."""
+    return _MacroscopicAfter.apply(F, f0, solver, int(nsteps), int(every))
 
 
 def kinetic_energy_after(solver, F, nsteps, every=20):

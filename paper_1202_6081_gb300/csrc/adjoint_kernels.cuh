@@ -155,6 +155,44 @@ __global__ void __launch_bounds__(128) energy_seed_kernel(const T *__restrict__ 
     }
 }
 
+// Seed of the adjoint for an objective J(rho, u) of the macroscopic fields
+// (Eqs. densitycalculation, velocitycalculation) given g_rho = dJ/drho and
+// g_u = dJ/du per cell (dense FP32; NULL = zero): since d rho / d f_a = 1 and
+// d u_i / d f_a = (e_ai - u_i) / rho,
+//     lam_a = g_rho + sum_i (e_ai - u_i) g_u_i / rho,
+// and the direct term dJ/dF_i += g_u_i / (2 rho) (u carries F/2).
+template <typename T>
+__global__ void __launch_bounds__(128) macro_seed_kernel(const T *__restrict__ buf,
+                                                         const StepArgs a, AdjointArgs g,
+                                                         const float *__restrict__ g_rho,
+                                                         const float *__restrict__ g_u) {
+    int x, y, z;
+    if (!cell_coords(a.g, x, y, z)) return;
+    float f[27];
+    gather<27, T>(buf, a.g, pull_sources(a.g, x, y, z), f);
+    float drho, jx, jy, jz, Fx, Fy, Fz;
+    moments<27>(f, drho, jx, jy, jz);
+    const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
+    const long long c = dense_index(a.g, x, y, z);
+    cell_force(a, c, N, Fx, Fy, Fz);
+    const float ir = 1.0f / (1.0f + drho);
+    const float ux = (jx + 0.5f * Fx) * ir, uy = (jy + 0.5f * Fy) * ir, uz = (jz + 0.5f * Fz) * ir;
+    const float gr = g_rho ? g_rho[c] : 0.0f;
+    const float gx = g_u ? g_u[c] * ir : 0.0f;
+    const float gy = g_u ? g_u[N + c] * ir : 0.0f;
+    const float gz = g_u ? g_u[2 * N + c] * ir : 0.0f;
+    const float base = gr - (ux * gx + uy * gy + uz * gz);
+    const long long own = ((long long)z * a.g.ny + y) * a.g.px + x;
+#pragma unroll
+    for (int q = 0; q < 27; ++q)
+        g.lam_out[q][own] = base + ex<27>(q) * gx + ey<27>(q) * gy + ez<27>(q) * gz;
+    if (g.gF) {
+        g.gF[c] += 0.5f * gx;
+        g.gF[N + c] += 0.5f * gy;
+        g.gF[2 * N + c] += 0.5f * gz;
+    }
+}
+
 // Per-block partial sums of rho |u|^2 / 2 (slot 0 of each 4-double record),
 // rows assigned to blocks as in the conservation reduction.
 template <int Q, typename T>
@@ -236,6 +274,20 @@ cudaError_t launch_energy_seed(const void *f, float *lam_out, float *gF, const S
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_macro_seed(const void *f, const float *g_rho, const float *g_u,
+                              float *lam_out, float *gF, const StepArgs &a, cudaStream_t st) {
+    AdjointArgs g;
+    for (int q = 0; q < 27; ++q) {
+        g.lam_next[q] = nullptr;
+        g.lam_out[q] = lam_out + q * a.g.pop;
+    }
+    g.gF = gF;
+    const CellLaunch L = cell_launch(a.g);
+    macro_seed_kernel<T><<<L.grid, L.block, 0, st>>>(static_cast<const T *>(f), a, g, g_rho, g_u);
+    return cudaGetLastError();
+}
+
 template <int Q, typename T>
 cudaError_t launch_energy(const void *f, const StepArgs &a, double *part, int blocks,
                           cudaStream_t st) {
@@ -248,6 +300,9 @@ cudaError_t launch_energy(const void *f, const StepArgs &a, double *part, int bl
                                                const StepArgs &, cudaStream_t);                 \
     EXT template cudaError_t launch_energy_seed<T>(const void *, float *, float *,               \
                                                    const StepArgs &, cudaStream_t);             \
+    EXT template cudaError_t launch_macro_seed<T>(const void *, const float *, const float *,    \
+                                                  float *, float *, const StepArgs &,           \
+                                                  cudaStream_t);                                \
     EXT template cudaError_t launch_energy<27, T>(const void *, const StepArgs &, double *, int, \
                                                   cudaStream_t);                                \
     EXT template cudaError_t launch_energy<15, T>(const void *, const StepArgs &, double *, int, \

@@ -99,6 +99,13 @@ struct SeedFn {
         return lbm::launch_energy_seed<T>(f, lo, gF, a, s);
     }
 };
+template <typename T>
+struct MacroSeedFn {
+    static cudaError_t run(const void *f, const float *g_rho, const float *g_u, float *lo,
+                           float *gF, const lbm::StepArgs &a, cudaStream_t s) {
+        return lbm::launch_macro_seed<T>(f, g_rho, g_u, lo, gF, a, s);
+    }
+};
 template <int Q, typename T>
 struct EnergyFn {
     static cudaError_t run(const void *f, const lbm::StepArgs &a, double *part, int blocks,
@@ -428,6 +435,27 @@ lbm_status lbm_kinetic_energy_seed(lbm_ctx *c, const void *f, float *lam_out, fl
     if (!state_buffer_ok(f) || (reinterpret_cast<uintptr_t>(lam_out) & 15u)) return LBM_EINVAL;
     if (c->Q != 27) return LBM_EUNSUPPORTED;
     cudaError_t e = dispatch_storage<SeedFn>(c, f, lam_out, dJdF, a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return LBM_OK;
+}
+
+lbm_status lbm_macroscopic_seed(lbm_ctx *c, const void *f, const float *g_rho, const float *g_u,
+                                float *lam_out, float *dJdF, void *stream) {
+    if (!c || !lam_out) return LBM_EINVAL;
+    lbm::StepArgs a = step_args(c);
+    if (!f) {
+        if (!c->bound || !c->state_set) return LBM_ESTATE;
+        f = c->buf[c->cur];
+    } else {
+        a.g.layout = lbm::kPull;  // a caller's buffer holds a two-buffer state
+    }
+    if (!state_buffer_ok(f) || (reinterpret_cast<uintptr_t>(lam_out) & 15u)) return LBM_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(g_rho) | reinterpret_cast<uintptr_t>(g_u) |
+         reinterpret_cast<uintptr_t>(dJdF)) & 3u)
+        return LBM_EINVAL;
+    if (c->Q != 27) return LBM_EUNSUPPORTED;
+    cudaError_t e = dispatch_storage<MacroSeedFn>(c, f, g_rho, g_u, lam_out, dJdF, a,
+                                                  (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     return LBM_OK;
 }

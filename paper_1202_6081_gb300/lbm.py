@@ -83,6 +83,7 @@ def load():
             "lbm_kinetic_energy": ([vp, vp, dp, vp], ip),
             "lbm_kinetic_energy_seed": ([vp, vp, vp, vp, vp], ip),
             "lbm_conservation_noalloc": ([vp, vp, vp], ip),
+            "lbm_macroscopic_seed": ([vp, vp, vp, vp, vp, vp, vp], ip),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -101,7 +102,8 @@ def exported_symbols():
               "lbm_set_state", "lbm_get_state", "lbm_step", "lbm_macroscopic",
               "lbm_conservation", "lbm_status_string", "lbm_last_cuda_error",
               "lbm_adjoint_bytes", "lbm_current_state", "lbm_step_into", "lbm_adjoint_step",
-              "lbm_kinetic_energy", "lbm_kinetic_energy_seed", "lbm_conservation_noalloc"):
+              "lbm_kinetic_energy", "lbm_kinetic_energy_seed", "lbm_conservation_noalloc",
+              "lbm_macroscopic_seed"):
         getattr(lib, n)
         names.append(n)
     return names
@@ -242,6 +244,11 @@ def lbm_kinetic_energy_seed(ctx, f, lam_out, dJdF=None, stream=None):
                                           _stream(stream)), "lbm_kinetic_energy_seed", ctx)
 
 
+def lbm_macroscopic_seed(ctx, f, g_rho, g_u, lam_out, dJdF=None, stream=None):
+    _check(load().lbm_macroscopic_seed(ctx, _ptr(f), _ptr(g_rho), _ptr(g_u), _ptr(lam_out),
+                                       _ptr(dJdF), _stream(stream)), "lbm_macroscopic_seed", ctx)
+
+
 # ---- convenience owner ----------------------------------------------------
 
 class Solver:
@@ -377,6 +384,14 @@ class Solver:
 
     def kinetic_energy_seed(self, buf, lam_out, dJdF=None, stream=None):
         lbm_kinetic_energy_seed(self.ctx, buf, lam_out, dJdF, stream)
+
+    def macroscopic_seed(self, buf, g_rho, g_u, lam_out, dJdF=None, stream=None):
+        """lam_out = dJ/df of the state in `buf` for J(rho, u) with the given
+        gradients (dense FP32 tensors, or None for zero)."""
+        g_rho = None if g_rho is None else g_rho.to(self.device, torch.float32).contiguous()
+        g_u = None if g_u is None else g_u.to(self.device, torch.float32).contiguous()
+        lbm_macroscopic_seed(self.ctx, buf, g_rho, g_u, lam_out, dJdF, stream)
+        self._keep = (g_rho, g_u)
 
     def adjoint_view(self, lam):
         """Dense [Q, nz, ny, nx] view of a pitched adjoint field."""

@@ -172,3 +172,82 @@ def test_gradient_128cubed_matches_gpu_finite_differences(lbm):
     fd, got = np.array(fd), np.array(got)
     print("fd", fd[:4], "adjoint", got[:4])
     assert np.abs(got - fd).max() <= 1e-3 * np.abs(fd).max()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_macroscopic_seed_matches_oracle(lbm, orc, storage):
+    """Seed of the adjoint for an objective J(rho, u): lam = dJ/df and the
+    direct dJ/dF against the oracle's chain rule, walled grid, force field."""
+    Q = 27
+    shape = (5, 7, 10)
+    rho, u = W.taylor_green(shape, u0=0.05, noise=1e-2, seed=51)
+    F = f32(W.rng(52).uniform(-1e-3, 1e-3, (3,) + shape))
+    g_rho = f32(W.rng(53).standard_normal(shape))
+    g_u = f32(W.rng(54).standard_normal((3,) + shape))
+    S = lbm.Solver(Q, shape, W.omegas(Q, 1.3), force=F, walls=3, storage=storage)
+    S.init_equilibrium(rho, u)
+    f = S.get_state().cpu().numpy()
+    lam = S.new_adjoint_field()
+    gF = torch.zeros((3,) + shape, dtype=torch.float32, device="cuda")
+    S.macroscopic_seed(S.current_buffer(), torch.as_tensor(g_rho, dtype=torch.float32),
+                       torch.as_tensor(g_u, dtype=torch.float32), lam, gF)
+    torch.cuda.synchronize()
+    want, want_F = orc.macroscopic_grad(Q, f, F, g_rho, g_u)
+    got = S.adjoint_view(lam).cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
+    assert np.abs(gF.cpu().numpy() - want_F).max() <= 1e-5 * np.abs(want_F).max()
+    # a missing gradient counts as zero
+    S.macroscopic_seed(S.current_buffer(), None, torch.as_tensor(g_u, dtype=torch.float32), lam)
+    torch.cuda.synchronize()
+    want0, _ = orc.macroscopic_grad(Q, f, F, 0.0, g_u)
+    assert np.abs(S.adjoint_view(lam).cpu().numpy() - want0).max() <= 1e-5 * np.abs(want0).max()
+
+
+def test_macroscopic_after_gradients_match_fp64_differences(lbm, orc):
+    """A torch objective of the final (rho, u), J = <c, u> + <d, rho^2>, back-
+    propagated through 30 steps (checkpoints every 7, so the last segment is
+    short) on a walled 6 x 8 x 10 grid: dJ/dF and dJ/df0 match FP64 central
+    differences of the oracle on 12 sampled entries each."""
+    from paper_1202_6081_gb300.autograd import macroscopic_after
+    Q = 27
+    shape = (6, 8, 10)
+    om = W.omegas(Q, 1 / 0.7)
+    rho0, u0 = W.taylor_green(shape, u0=0.03, noise=2e-3, seed=55)
+    F0 = f32(W.rng(56).uniform(-1e-4, 1e-4, (3,) + shape))
+    f0 = orc.equilibrium(Q, rho0, u0, F0)
+    c = torch.as_tensor(W.rng(57).standard_normal((3,) + shape), dtype=torch.float32,
+                        device="cuda")
+    d = torch.as_tensor(W.rng(58).standard_normal(shape), dtype=torch.float32, device="cuda")
+    S = lbm.Solver(Q, shape, om, walls=3)
+    Ft = torch.as_tensor(F0, dtype=torch.float32, device="cuda").contiguous().requires_grad_()
+    f0t = torch.as_tensor(f0, device="cuda").requires_grad_()
+    rho, u = macroscopic_after(S, Ft, 30, every=7, f0=f0t)
+    J = (c * u).sum() + (d * rho * rho).sum()
+    J.backward()
+    gF, gf0 = Ft.grad.cpu().numpy(), f0t.grad.cpu().numpy()
+    cn, dn = c.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64)
+
+    def J_or(f_init, F):
+        r, v = orc.macroscopic(Q, orc.run(Q, shape, f_init, F, om, 30, bc=3), F)
+        return np.sum(cn * v) + np.sum(dn * r * r)
+
+    rng = W.rng(59)
+    eps = 1e-6
+    fdF, gotF, fdf, gotf = [], [], [], []
+    for _ in range(12):
+        k, z, y, x = (int(rng.integers(0, n)) for n in (3,) + shape)
+        Fp, Fm = F0.copy(), F0.copy()
+        Fp[k, z, y, x] += eps
+        Fm[k, z, y, x] -= eps
+        fdF.append((J_or(f0, Fp) - J_or(f0, Fm)) / (2 * eps))
+        gotF.append(gF[k, z, y, x])
+        a = int(rng.integers(0, Q))
+        fp, fm = f0.copy(), f0.copy()
+        fp[a, z, y, x] += eps
+        fm[a, z, y, x] -= eps
+        fdf.append((J_or(fp, F0) - J_or(fm, F0)) / (2 * eps))
+        gotf.append(gf0[a, z, y, x])
+    fdF, gotF, fdf, gotf = map(np.array, (fdF, gotF, fdf, gotf))
+    print("dJ/dF fd", fdF[:3], "adjoint", gotF[:3], "; dJ/df0 fd", fdf[:3], "adjoint", gotf[:3])
+    assert np.abs(gotF - fdF).max() <= 1e-3 * np.abs(fdF).max()
+    assert np.abs(gotf - fdf).max() <= 1e-3 * np.abs(fdf).max()

@@ -236,6 +236,30 @@ def test_16bit_storage_taylor_green(lbm, orc, storage, bound):
     assert err <= bound
 
 
+@pytest.mark.parametrize("Q", [27, 15])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("shape", [(6, 11, 35), (6, 11, 36)])  # one-cell and two-cell kernels
+def test_16bit_storage_walled_channel(lbm, orc, Q, storage, shape):
+    """Both step kernels' stochastically rounded 16-bit stores (odd nx: one
+    cell per thread; even nx: pairs) on a walled channel with a force field:
+    velocity after 40 steps against the FP64 oracle, relative L2 within the
+    16-bit bounds (1e-3 FP16, 5e-3 BF16)."""
+    om = W.omegas(Q, 1.25)
+    F = W.rng(15).uniform(-1e-4, 1e-4, (3,) + shape) + np.array([1e-4, 0, 0])[:, None, None,
+                                                                              None]
+    F32 = F.astype(np.float32).astype(np.float64)
+    rho0, u0 = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    S = lbm.Solver(Q, shape, om, force=F, walls=3, storage=storage)
+    S.init_equilibrium(rho0, u0)
+    S.step(40)
+    f_or = orc.run(Q, shape, orc.equilibrium(Q, rho0, u0, F32), F32, om, 40, bc=3)
+    _, u_g = orc.macroscopic(Q, gpu_state(S), F32)
+    _, u_o = orc.macroscopic(Q, f_or, F32)
+    err = rel_l2(u_g, u_o)
+    print("D3Q%d %s %s: rel L2 u = %.3e" % (Q, storage, shape, err))
+    assert err <= (1e-3 if storage == "f16" else 5e-3)
+
+
 @pytest.fixture(scope="module")
 def tgv64_oracle(orc):
     """The FP64 oracle on the Taylor-Green + noise flow at 64^3, tau = 0.6,

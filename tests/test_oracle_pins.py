@@ -293,6 +293,43 @@ def test_adjoint_step_is_the_transpose_of_the_linearised_step(oracle_lib, Q, bc)
 
 
 @pytest.mark.parametrize("Q", [27, 15])
+def test_macroscopic_grad_matches_differences(oracle_lib, Q):
+    """The chain rule through Eqs. densitycalculation and velocitycalculation
+    (seed of the adjoint for an objective of rho and u) equals central
+    differences of J = <g_rho, rho> + <g_u, u> in every population and force
+    component, and for J = sum rho |u|^2 / 2 it reduces to the kinetic-energy
+    seed u.e - |u|^2 / 2, u / 2."""
+    shape = (2, 3, 2)
+    rng = W.rng(25)
+    f = W.random_field_state(shape, Q, seed=26, spread=0.4)
+    F = rng.uniform(-1e-2, 1e-2, (3,) + shape)
+    g_rho = rng.standard_normal(shape)
+    g_u = rng.standard_normal((3,) + shape)
+    dfl, dF = oracle_lib.macroscopic_grad(Q, f, F, g_rho, g_u)
+
+    def J(ff, FF):
+        rho, u = oracle_lib.macroscopic(Q, ff, FF)
+        return np.sum(g_rho * rho) + np.sum(g_u * u)
+
+    h = 1e-6
+    for idx in np.ndindex(f.shape):
+        fp, fm = f.copy(), f.copy()
+        fp[idx] += h
+        fm[idx] -= h
+        assert dfl[idx] == pytest.approx((J(fp, F) - J(fm, F)) / (2 * h), rel=1e-7, abs=1e-8)
+    for idx in np.ndindex(F.shape):
+        Fp, Fm = F.copy(), F.copy()
+        Fp[idx] += h
+        Fm[idx] -= h
+        assert dF[idx] == pytest.approx((J(f, Fp) - J(f, Fm)) / (2 * h), rel=1e-7, abs=1e-8)
+    rho, u = oracle_lib.macroscopic(Q, f, F)
+    ke_f, ke_F = oracle_lib.kinetic_energy_grad(Q, f, F)
+    mg_f, mg_F = oracle_lib.macroscopic_grad(Q, f, F, 0.5 * np.sum(u * u, axis=0), rho * u)
+    np.testing.assert_allclose(mg_f, ke_f, atol=1e-14)
+    np.testing.assert_allclose(mg_F, ke_F, atol=1e-14)
+
+
+@pytest.mark.parametrize("Q", [27, 15])
 def test_streaming_moves_and_bounces(oracle_lib, Q):
     """Eq. cascadedstreaming1 with a collision that is the identity (all rates
     zero, no force): each population moves one link; at a wall it comes back
