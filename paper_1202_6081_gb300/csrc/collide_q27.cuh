@@ -259,6 +259,152 @@ __device__ __forceinline__ void inverse27(V (&D)[3][3][3], V ux, V uy, V uz, V (
                               f[s27(1, j, k)], f[s27(2, j, k)]);
 }
 
+// ---- lean variant for the two-cell kernels ------------------------------
+//
+// (1) The inverse sweeps leave out the factors 1/2 of dist_from_central: the
+//     three inputs of every line share one power-of-two factor, so each
+//     output f(i, j, k) comes out multiplied by G_i G_j G_k (G = 2, 1, 2 for
+//     e = -1, 0, +1), exactly, and the kernel folds 1 / (G_i G_j G_k) into
+//     the one multiplication it applies at the store anyway (FP32: exact
+//     powers of two, so the stored values are bit-identical).
+// (2) For storage of s = (f - w) / w the forward sweeps fold the weights in:
+//     w = W_i W_j W_k / 216 with W = (1, 4, 1), so a + 4 b + c along each
+//     axis gives 216 times the moments of the deviations with no per-value
+//     multiplication.  The relaxation is linear in the pre-collision moments
+//     (c~ = (1 - omega) c + omega c^eq), so dividing 1 - omega by 216 on the
+//     host (packed_rates) relaxes the scaled moments correctly; only the
+//     invariant moments (orders 0 and 1) are scaled back explicitly.
+
+// G_i G_j G_k of slot q
+__host__ __device__ constexpr int g27(int q) {
+    return (q27_e(q, 0) ? 2 : 1) * (q27_e(q, 1) ? 2 : 1) * (q27_e(q, 2) ? 2 : 1);
+}
+
+template <typename V>
+__device__ __forceinline__ void dist_from_central_g(V u, V k0, V k1, V k2, V &a, V &b, V &c) {
+    const V m1 = vfma(u, k0, k1);
+    const V m2 = vfma(u, k1 + m1, k2);
+    b = k0 - m2;
+    c = m2 + m1;
+    a = m2 - m1;
+}
+
+template <typename V>
+__device__ __forceinline__ void inverse27_g(V (&D)[3][3][3], V ux, V uy, V uz, V (&f)[27]) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            V a, b, c;
+            dist_from_central_g(uz, D[m][n][0], D[m][n][1], D[m][n][2], a, b, c);
+            D[m][n][0] = a;
+            D[m][n][1] = b;
+            D[m][n][2] = c;
+        }
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            V a, b, c;
+            dist_from_central_g(uy, D[m][0][k], D[m][1][k], D[m][2][k], a, b, c);
+            D[m][0][k] = a;
+            D[m][1][k] = b;
+            D[m][2][k] = c;
+        }
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            dist_from_central_g(ux, D[0][j][k], D[1][j][k], D[2][j][k], f[s27(0, j, k)],
+                                f[s27(1, j, k)], f[s27(2, j, k)]);
+}
+
+// weighted raw sums of the line (a, b, c) = (s(-1), s(0), s(+1)), weights (1, 4, 1)
+template <typename V>
+__device__ __forceinline__ void sums_w(V a, V b, V c, V &s0, V &s1, V &s2) {
+    const V ac = a + c;
+    s0 = vfma(splat<V>(4.0f), b, ac);
+    s1 = c - a;
+    s2 = ac;
+}
+
+// Forward transform of weight-scaled values s (f - w = w s): D = 216 x the
+// central moments of the deviations for orders >= 2, the true ones for
+// orders 0 and 1; drho and u as in forward27.
+template <typename V>
+__device__ __forceinline__ void forward27_w(const V (&s)[27], V (&D)[3][3][3], V Fx, V Fy, V Fz,
+                                            V &drho, V &ux, V &uy, V &uz) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            sums_w(s[s27(0, j, k)], s[s27(1, j, k)], s[s27(2, j, k)], D[0][j][k], D[1][j][k],
+                   D[2][j][k]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            V s0, s1, s2;
+            sums_w(D[m][0][k], D[m][1][k], D[m][2][k], s0, s1, s2);
+            D[m][0][k] = s0;
+            D[m][1][k] = s1;
+            D[m][2][k] = s2;
+        }
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            V s0, s1, s2;
+            sums_w(D[m][n][0], D[m][n][1], D[m][n][2], s0, s1, s2);
+            D[m][n][0] = s0;
+            D[m][n][1] = s1;
+            D[m][n][2] = s2;
+        }
+    const V half = splat<V>(0.5f), inv216 = splat<V>(1.0f / 216.0f);
+    drho = D[0][0][0] * inv216;
+    const V inv_rho = vrcp(splat<V>(1.0f) + drho);
+    ux = vfma(D[1][0][0], inv216, half * Fx) * inv_rho;
+    uy = vfma(D[0][1][0], inv216, half * Fy) * inv_rho;
+    uz = vfma(D[0][0][1], inv216, half * Fz) * inv_rho;
+    const V zero = splat<V>(0.0f);
+    const V nux = zero - ux, nuy = zero - uy, nuz = zero - uz;
+#pragma unroll
+    for (int n = 0; n < 3; ++n)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) central_from_sums(nux, D[0][n][p], D[1][n][p], D[2][n][p]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) central_from_sums(nuy, D[m][0][p], D[m][1][p], D[m][2][p]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int n = 0; n < 3; ++n) central_from_sums(nuz, D[m][n][0], D[m][n][1], D[m][n][2]);
+    // the collision invariants are not relaxed: back to true scale
+    D[0][0][0] = drho;
+    D[1][0][0] = D[1][0][0] * inv216;
+    D[0][1][0] = D[0][1][0] * inv216;
+    D[0][0][1] = D[0][0][1] * inv216;
+}
+
+// The collision of collide27 with outputs G_i G_j G_k f~ (see (1) above);
+// kWeighted: inputs are weight-scaled values s and r.omw holds
+// (1 - omega) / 216 (see (2) above).
+template <typename V, bool kWeighted>
+__device__ __forceinline__ void collide27_g(V (&f)[27], V Fx, V Fy, V Fz, const Rates27<V> &r) {
+    V D[3][3][3];
+    V drho, ux, uy, uz;
+    if constexpr (kWeighted)
+        forward27_w(f, D, Fx, Fy, Fz, drho, ux, uy, uz);
+    else
+        forward27(f, D, Fx, Fy, Fz, drho, ux, uy, uz);
+    D[1][0][0] = D[1][0][0] + Fx;
+    D[0][1][0] = D[0][1][0] + Fy;
+    D[0][0][1] = D[0][0][1] + Fz;
+    relax27(D, ux, uy, uz, drho, r);
+    inverse27_g(D, ux, uy, uz, f);
+}
+
 // One cell (or a pair of cells, V = f2): pre-collision deviations in,
 // post-collision deviations out (both f - w, slot order).
 template <typename V>

@@ -213,6 +213,22 @@ __device__ __forceinline__ Rates27<f2> load_rates_packed(const PackedRates &p) {
     return r;
 }
 
+// Factors of the two-cell kernels between stored values and the collision's
+// values.  D3Q27 uses collide27_g: 16-bit inputs go in as stored (the
+// weights are folded into its sums), and outputs carry G_i G_j G_k.
+template <int Q, typename T>
+__host__ __device__ constexpr bool kFoldedLoad() {
+    return Q == 27 && Storage<T>::kScaled;
+}
+template <int Q, typename T>
+__host__ __device__ constexpr float load_scale(int q) {
+    return (Storage<T>::kScaled && Q != 27) ? float(weight<Q>(q)) : 1.0f;
+}
+template <int Q, typename T>
+__host__ __device__ constexpr float store_scale(int q) {
+    return float((Storage<T>::kScaled ? 1.0 / weight<Q>(q) : 1.0) / (Q == 27 ? g27(q) : 1));
+}
+
 // Row offsets (elements) of the 3 x 3 source rows of a pull, for cell row
 // (y, z); wall[j][k] set where that source is beyond a bounce-back wall.
 template <bool kWalls>
@@ -305,7 +321,7 @@ __global__ void __launch_bounds__(128) step2_kernel(const StepIO<T> io, const St
             else
                 v = f2(Pair<T>::ld1(row + x0 + 1), Pair<T>::ld1(row + xp));
         }
-        f[q] = Storage<T>::kScaled ? v * f2(float(weight<27>(q))) : v;
+        f[q] = v;  // weight-scaled 16-bit values go in as stored (collide27_g)
     }
     f2 Fx, Fy, Fz;
     if (a.Ffield) {
@@ -320,10 +336,11 @@ __global__ void __launch_bounds__(128) step2_kernel(const StepIO<T> io, const St
         Fz = f2(a.F[2]);
     }
     const Rates27<f2> r = load_rates_packed(pr);
-    collide27<f2>(f, Fx, Fy, Fz, r);
+    collide27_g<f2, Storage<T>::kScaled>(f, Fx, Fy, Fz, r);
     static_for<27>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
-        const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<27>(q))) : f[q];
+        constexpr float sc = store_scale<27, T>(q);
+        const f2 v = sc == 1.0f ? f[q] : f[q] * f2(sc);
         Pair<T>::template st2s<q>(io.out[q] + R.own + x0, v, sr_salt(R.own + x0));
     });
 }
@@ -398,14 +415,16 @@ template <int Q>
 struct PairCollide;
 template <>
 struct PairCollide<27> {
+    template <bool kWeighted>
     __device__ __forceinline__ static void run(f2 (&f)[27], f2 Fx, f2 Fy, f2 Fz,
                                                const PackedRates &pr, bool) {
         const Rates27<f2> r = load_rates_packed(pr);
-        collide27<f2>(f, Fx, Fy, Fz, r);
+        collide27_g<f2, kWeighted>(f, Fx, Fy, Fz, r);
     }
 };
 template <>
 struct PairCollide<15> {
+    template <bool>
     __device__ __forceinline__ static void run(f2 (&f)[15], f2 Fx, f2 Fy, f2 Fz,
                                                const PackedRates &pr, bool has_force) {
         Rates15<f2> r;
@@ -441,15 +460,17 @@ __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const 
     f2 f[Q];
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
+        constexpr float sc = load_scale<Q, T>(q);
         const f2 v = Pair<T>::ld2(io.in[q] + own);
-        f[q] = Storage<T>::kScaled ? v * f2(float(weight<Q>(q))) : v;
+        f[q] = sc == 1.0f ? v : v * f2(sc);
     });
     f2 Fx, Fy, Fz;
     pair_force(a, x0, y, z, Fx, Fy, Fz);
-    PairCollide<Q>::run(f, Fx, Fy, Fz, pr, a.has_force != 0);
+    PairCollide<Q>::template run<kFoldedLoad<Q, T>()>(f, Fx, Fy, Fz, pr, a.has_force != 0);
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
-        const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<Q>(q))) : f[q];
+        constexpr float sc = store_scale<Q, T>(q);
+        const f2 v = sc == 1.0f ? f[q] : f[q] * f2(sc);
         Pair<T>::template st2s<q>(io.out[opposite<Q>(q)] + own, v, sr_salt(own));
     });
 }
@@ -482,16 +503,18 @@ __global__ void __launch_bounds__(128) aa_odd_kernel(const StepIO<T> io, const S
             else
                 v = f2(Pair<T>::ld1(row + x0 + 1), Pair<T>::ld1(row + xp));
         }
-        f[q] = Storage<T>::kScaled ? v * f2(float(weight<Q>(q))) : v;
+        constexpr float sc = load_scale<Q, T>(q);
+        f[q] = sc == 1.0f ? v : v * f2(sc);
     });
     f2 Fx, Fy, Fz;
     pair_force(a, x0, y, z, Fx, Fy, Fz);
-    PairCollide<Q>::run(f, Fx, Fy, Fz, pr, a.has_force != 0);
+    PairCollide<Q>::template run<kFoldedLoad<Q, T>()>(f, Fx, Fy, Fz, pr, a.has_force != 0);
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
         constexpr int i = ex<Q>(q), j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
         constexpr int o = opposite<Q>(q);
-        const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<Q>(q))) : f[q];
+        constexpr float sc = store_scale<Q, T>(q);
+        const f2 v = sc == 1.0f ? f[q] : f[q] * f2(sc);
         // downstream neighbour x + e_q: the row of the mirrored pull
         const unsigned salt = sr_salt(own);
         if (kWalls && R.wall[2 - j][2 - k]) {
@@ -641,11 +664,13 @@ inline unsigned long long splat_bits(float v) {
     return (unsigned long long)u << 32 | u;
 }
 
-inline PackedRates packed_rates(const StepArgs &a) {
+// weighted: for collide27_g on weight-scaled inputs, (1 - omega) / 216.
+inline PackedRates packed_rates(const StepArgs &a, bool weighted = false) {
     PackedRates p;
     for (int b = 0; b < 15; ++b) p.w15[b] = splat_bits(a.w[b] * k15_inv(b));
     for (int b = 0; b < 27; ++b) {
-        const float w = a.w[b], nw = -a.w[b], omw = 1.0f - a.w[b];
+        const float w = a.w[b], nw = -a.w[b];
+        const float omw = weighted ? (1.0f - a.w[b]) / 216.0f : 1.0f - a.w[b];
         unsigned int uw, unw, uomw;
         memcpy(&uw, &w, 4);
         memcpy(&unw, &nw, 4);
@@ -672,7 +697,7 @@ cudaError_t launch_step(const void *fin, void *fout, const StepArgs &a, cudaStre
             Grid half = a.g;
             half.nx = a.g.nx / 2;
             const CellLaunch L = cell_launch(half);
-            const PackedRates pr = packed_rates(a);
+            const PackedRates pr = packed_rates(a, kFoldedLoad<27, T>());
             if (walls)
                 step2_kernel<T, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
             else
@@ -714,7 +739,7 @@ cudaError_t launch_step_aa(void *buf, const StepArgs &a, bool even, cudaStream_t
     Grid half = a.g;
     half.nx = a.g.nx / 2;
     const CellLaunch L = cell_launch(half);
-    const PackedRates pr = packed_rates(a);
+    const PackedRates pr = packed_rates(a, kFoldedLoad<Q, T>());
     if (even)
         aa_even_kernel<Q, T><<<L.grid, L.block, 0, st>>>(io, a, pr);
     else if (a.g.bc)
