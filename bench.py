@@ -371,6 +371,29 @@ def adjoint_timing(torch, lbm, size, steps=100):
                                    "backward_forward_ratio": (t2 - t1) / (t1 - t0)}}
 
 
+def small_grids(torch, lbm, steps=4000):
+    """Small grids are bound by launch cost: D3Q27 FP32 MLUPS with every step
+    launched on its own and with runs of 32 steps launched as CUDA graphs."""
+    import workloads as W
+    out = {}
+    om = W.omegas(27, 1 / 0.6)
+    for name, shape, walls in (("32^3 periodic", (32, 32, 32), 0),
+                               ("16x64x64 channel", (64, 64, 16), 3),
+                               ("64^3 periodic", (64, 64, 64), 0),
+                               ("128^3 periodic", (128, 128, 128), 0)):
+        rho, u = W.taylor_green(shape, u0=0.02, noise=1e-3)
+        row = {}
+        for gs in (0, 32):
+            S = lbm.Solver(27, shape, om, walls=walls)
+            S.set_graph_steps(gs)
+            S.init_equilibrium(rho, u)
+            t = time_steps(torch, S, steps, 64)
+            row["graphs" if gs else "single_launches"] = int(np.prod(shape)) * steps / t / 1e6
+            del S
+        out[name] = row
+    return out
+
+
 def max_over_ranks(torch, value, device):
     """The largest value over the ranks of the default process group (the
     slowest rank's time).  Timing only: no simulation data is exchanged."""
@@ -480,6 +503,7 @@ def run_ours(args):
             del S
             torch.cuda.empty_cache()
         result["inplace_aa"] = aa
+        result["small_grids"] = small_grids(torch, lbm)
         result["adjoint"] = adjoint_timing(torch, lbm, 128)
         torch.cuda.empty_cache()
         result["cpu_baseline"] = cpu_baseline(size)

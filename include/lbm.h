@@ -162,9 +162,19 @@ lbm_status lbm_get_state(const lbm_ctx *ctx, double *f, void *stream);
 
 /* Advance nsteps >= 0 fused collide-and-stream steps (Eqs. cascadedcollision1
  * and cascadedstreaming1), one kernel launch per step on `stream` (with
- * LBM_INPLACE, alternately the in-place and the neighbour kernel).
+ * LBM_INPLACE, alternately the in-place and the neighbour kernel).  Runs of
+ * lbm_set_graph_steps steps (32 by default) are launched as one CUDA graph,
+ * captured on first use for the current force, rates, buffers and parity
+ * and replayed while those stay the same; the rest step by step.  Inside a
+ * stream capture of the caller's, every step is launched on its own.
  * Errors: LBM_ESTATE (not bound), LBM_EINVAL (nsteps < 0), LBM_ECUDA. */
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps, void *stream);
+
+/* Steps per CUDA graph in lbm_step: an even count >= 2, or 0 to launch every
+ * step on its own (graphs cut the host's launch cost, which bounds small
+ * grids).  Results do not depend on it.  Not in the paper.
+ * Errors: LBM_EINVAL (negative or odd). */
+lbm_status lbm_set_graph_steps(lbm_ctx *ctx, int steps);
 
 /* Density and velocity of the current state, Eqs. densitycalculation and
  * velocitycalculation (u includes the +F/2 shift):

@@ -16,6 +16,21 @@ LBM_INSTANTIATE_ADJOINT(extern, __half)
 LBM_INSTANTIATE_ADJOINT(extern, __nv_bfloat16)
 }  // namespace lbm
 
+// A captured run of steps (a CUDA graph), valid for the launch arguments,
+// buffers and starting parity in its key.
+struct GraphKey {
+    int Q, storage, nx, ny, nz, px, layout, cur, steps, has_force;
+    unsigned bc;
+    float w[27], F[3];
+    const float *Ffield;
+    const void *buf0, *buf1;
+};
+struct StepGraph {
+    GraphKey key;
+    cudaGraphExec_t exec;
+    unsigned long long used;  // for least-recently-used replacement
+};
+
 struct lbm_ctx {
     int Q;
     lbm_storage storage;
@@ -29,12 +44,18 @@ struct lbm_ctx {
     bool state_set;
     bool inplace;  // single-buffer (AA) streaming; g.layout tracks the state's layout
     int device;
+    int graph_steps;          // steps per captured graph; 0: launch each step
+    cudaStream_t cap_stream;  // private stream the graphs are captured on
+    StepGraph graphs[2];      // one per starting parity, typically
+    unsigned long long graph_clock;
     double *red_scratch;  // partial sums + 4 totals
     int red_blocks;
     const char *cuda_error;
 };
 
 namespace {
+
+constexpr int kDefaultGraphSteps = 32;
 
 size_t elem_bytes(lbm_storage st) { return st == LBM_STORE_F32 ? 4 : 2; }
 
@@ -58,6 +79,37 @@ bool valid_rates(int Q, const double *omega) {
 lbm_status cuda_fail(const lbm_ctx *c, cudaError_t e) {
     const_cast<lbm_ctx *>(c)->cuda_error = cudaGetErrorString(e);
     return LBM_ECUDA;
+}
+
+// Every field set one by one on a zeroed key, so keys compare bytewise.
+GraphKey graph_key(const lbm_ctx *c, int steps) {
+    GraphKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.Q = c->Q;
+    k.storage = int(c->storage);
+    k.nx = c->g.nx;
+    k.ny = c->g.ny;
+    k.nz = c->g.nz;
+    k.px = c->g.px;
+    k.layout = c->g.layout;
+    k.cur = c->cur;
+    k.steps = steps;
+    k.bc = c->g.bc;
+    for (int b = 0; b < 27; ++b) k.w[b] = c->w[b];
+    for (int i = 0; i < 3; ++i) k.F[i] = c->F[i];
+    k.Ffield = c->Ffield;
+    k.has_force = step_args(c).has_force;
+    k.buf0 = c->buf[0];
+    k.buf1 = c->buf[1];
+    return k;
+}
+
+void drop_graphs(lbm_ctx *c) {
+    for (StepGraph &g : c->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        g.used = 0;
+    }
 }
 
 // Dispatch on (Q, storage) to a templated launcher F<Q, T>.
@@ -205,6 +257,7 @@ lbm_status lbm_create(lbm_lattice lattice, int nx, int ny, int nz, const double 
     for (int i = 0; i < 3; ++i) c->F[i] = force ? float(force[i]) : 0.0f;
     c->cur = 0;
     c->device = dev;
+    c->graph_steps = kDefaultGraphSteps;
     c->cuda_error = "";
     *out = c;
     return LBM_OK;
@@ -212,6 +265,8 @@ lbm_status lbm_create(lbm_lattice lattice, int nx, int ny, int nz, const double 
 
 void lbm_destroy(lbm_ctx *c) {
     if (!c) return;
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->red_scratch) cudaFree(c->red_scratch);
     delete c;
 }
@@ -304,26 +359,99 @@ lbm_status lbm_get_state(const lbm_ctx *c, double *f, void *stream) {
     return LBM_OK;
 }
 
+// Enqueue n step launches on st, advancing the state parity in c.
+static cudaError_t enqueue_steps(lbm_ctx *c, int n, cudaStream_t st) {
+    for (int s = 0; s < n; ++s) {
+        const lbm::StepArgs a = step_args(c);
+        cudaError_t e;
+        if (c->inplace) {
+            const bool even = c->g.layout == lbm::kAANatural;
+            e = dispatch<StepAAFn>(c, c->buf[0], a, even, st);
+            c->g.layout = even ? lbm::kAASwapped : lbm::kAANatural;
+        } else {
+            e = dispatch<StepFn>(c, (const void *)c->buf[c->cur], c->buf[1 - c->cur], a, st);
+            c->cur = 1 - c->cur;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// The graph of c->graph_steps steps from the current arguments and parity,
+// captured on first use.  nullptr if capturing failed (the caller then
+// launches step by step; the failure leaves no error state behind).
+static StepGraph *graph_for(lbm_ctx *c) {
+    const GraphKey k = graph_key(c, c->graph_steps);
+    StepGraph *slot = &c->graphs[0];
+    for (StepGraph &g : c->graphs) {
+        if (g.exec && std::memcmp(&g.key, &k, sizeof(k)) == 0) {
+            g.used = ++c->graph_clock;
+            return &g;
+        }
+        if (g.used < slot->used) slot = &g;
+    }
+    if (!c->cap_stream &&
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->cap_stream = nullptr;
+        return nullptr;
+    }
+    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+    slot->exec = nullptr;
+    slot->used = 0;
+    // capture with a copy of the parity: the capture launches nothing
+    const int cur = c->cur, layout = c->g.layout;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t el = enqueue_steps(c, c->graph_steps, c->cap_stream);
+        e = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (e == cudaSuccess) e = el;
+    }
+    c->cur = cur;
+    c->g.layout = layout;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    slot->key = k;
+    slot->exec = exec;
+    slot->used = ++c->graph_clock;
+    return slot;
+}
+
 lbm_status lbm_step(lbm_ctx *c, int nsteps, void *stream) {
     if (!c || nsteps < 0) return LBM_EINVAL;
     if (!c->bound || !c->state_set) return LBM_ESTATE;
-    if (c->inplace) {
-        for (int s = 0; s < nsteps; ++s) {
-            const lbm::StepArgs a = step_args(c);
-            const bool even = c->g.layout == lbm::kAANatural;
-            cudaError_t e = dispatch<StepAAFn>(c, c->buf[0], a, even, (cudaStream_t)stream);
-            if (e != cudaSuccess) return cuda_fail(c, e);
-            c->g.layout = even ? lbm::kAASwapped : lbm::kAANatural;
+    cudaStream_t st = (cudaStream_t)stream;
+    int left = nsteps;
+    if (c->graph_steps > 0 && left >= c->graph_steps) {
+        // inside a caller's own stream capture, launch step by step
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            cs = cudaStreamCaptureStatusActive;
         }
-        return LBM_OK;
+        while (cs == cudaStreamCaptureStatusNone && left >= c->graph_steps) {
+            StepGraph *g = graph_for(c);
+            if (!g) break;
+            const cudaError_t e = cudaGraphLaunch(g->exec, st);
+            if (e != cudaSuccess) return cuda_fail(c, e);
+            left -= c->graph_steps;  // an even count: the parity is unchanged
+        }
     }
-    const lbm::StepArgs a = step_args(c);
-    for (int s = 0; s < nsteps; ++s) {
-        cudaError_t e = dispatch<StepFn>(c, (const void *)c->buf[c->cur], c->buf[1 - c->cur], a,
-                                         (cudaStream_t)stream);
-        if (e != cudaSuccess) return cuda_fail(c, e);
-        c->cur = 1 - c->cur;
-    }
+    const cudaError_t e = enqueue_steps(c, left, st);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_graph_steps(lbm_ctx *c, int steps) {
+    if (!c || steps < 0 || steps % 2 != 0) return LBM_EINVAL;
+    if (steps != c->graph_steps) drop_graphs(c);
+    c->graph_steps = steps;
     return LBM_OK;
 }
 

@@ -84,6 +84,7 @@ def load():
             "lbm_kinetic_energy_seed": ([vp, vp, vp, vp, vp], ip),
             "lbm_conservation_noalloc": ([vp, vp, vp], ip),
             "lbm_macroscopic_seed": ([vp, vp, vp, vp, vp, vp, vp], ip),
+            "lbm_set_graph_steps": ([vp, ip], ip),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -103,7 +104,7 @@ def exported_symbols():
               "lbm_conservation", "lbm_status_string", "lbm_last_cuda_error",
               "lbm_adjoint_bytes", "lbm_current_state", "lbm_step_into", "lbm_adjoint_step",
               "lbm_kinetic_energy", "lbm_kinetic_energy_seed", "lbm_conservation_noalloc",
-              "lbm_macroscopic_seed"):
+              "lbm_macroscopic_seed", "lbm_set_graph_steps"):
         getattr(lib, n)
         names.append(n)
     return names
@@ -244,6 +245,10 @@ def lbm_kinetic_energy_seed(ctx, f, lam_out, dJdF=None, stream=None):
                                           _stream(stream)), "lbm_kinetic_energy_seed", ctx)
 
 
+def lbm_set_graph_steps(ctx, steps):
+    _check(load().lbm_set_graph_steps(ctx, int(steps)), "lbm_set_graph_steps", ctx)
+
+
 def lbm_macroscopic_seed(ctx, f, g_rho, g_u, lam_out, dJdF=None, stream=None):
     _check(load().lbm_macroscopic_seed(ctx, _ptr(f), _ptr(g_rho), _ptr(g_u), _ptr(lam_out),
                                        _ptr(dJdF), _stream(stream)), "lbm_macroscopic_seed", ctx)
@@ -326,6 +331,10 @@ class Solver:
 
     def step(self, nsteps=1, stream=None):
         lbm_step(self.ctx, nsteps, stream)
+
+    def set_graph_steps(self, steps):
+        """Steps per CUDA graph in step() (even; 0 = one launch per step)."""
+        lbm_set_graph_steps(self.ctx, steps)
 
     def macroscopic(self, stream=None):
         rho = torch.empty(self.shape, dtype=torch.float32, device=self.device)
