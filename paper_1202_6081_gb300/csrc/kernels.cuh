@@ -20,15 +20,23 @@ struct StepArgs {
     int has_force;         // 0: no force anywhere (the source term vanishes)
 };
 
-// Launch geometry shared by the per-cell kernels: blocks of 128 threads laid
-// along x (whole warps on a row), several rows per block when nx is short.
+// Launch geometry shared by the per-cell kernels (cell_launch below).
 struct CellLaunch {
     dim3 grid, block;
 };
 
+// 128-thread blocks along x: rows of at least 17 threads take whole warps
+// (32, 64, 96 or 128 threads per row); shorter rows take the next power of
+// two, so that a warp covers several rows instead of idling.
 inline CellLaunch cell_launch(const Grid &g) {
-    int bx = ((g.nx + 31) / 32) * 32;
-    if (bx > 128) bx = 128;
+    int bx;
+    if (g.nx <= 16) {
+        bx = 1;
+        while (bx < g.nx) bx *= 2;
+    } else {
+        bx = ((g.nx + 31) / 32) * 32;
+        if (bx > 128) bx = 128;
+    }
     int by = 128 / bx;
     if (by < 1) by = 1;
     CellLaunch L;
