@@ -303,8 +303,11 @@ __global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const Ste
 // the collision in packed f32x2 arithmetic.  nx must be even.  Loads of
 // populations with e_x = 0 and all stores are aligned 2-element accesses;
 // e_x = +-1 sources are two single loads (x0 - 1, x0) or (x0 + 1, x0 + 2).
+// 5 blocks of 128 per SM: FP32 storage fits in 96 registers; 16-bit storage
+// spills 72 bytes there but runs faster than at 4 blocks (40.2k vs 38.0k
+// MLUPS FP16 at 512^3).
 template <typename T, bool kWalls>
-__global__ void __launch_bounds__(128) step2_kernel(const StepIO<T> io, const StepArgs a,
+__global__ void __launch_bounds__(128, 5) step2_kernel(const StepIO<T> io, const StepArgs a,
                                                     const PackedRates pr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
@@ -368,8 +371,13 @@ __device__ __forceinline__ f2 pull_pair(const StepIO<T> &io, const Rows<kWalls> 
 
 // One fused D3Q15 step, two neighbouring cells per thread in packed f32x2
 // arithmetic (nx even); loads and stores as in step2_kernel.
+// 16-bit storage: 5 blocks per SM (a few spilled registers) beat 4 (60.2k
+// vs 55.4k MLUPS at 256^3); FP32 storage is faster at 4 without spills.
+template <typename T>
+constexpr int kQ15Blocks = Storage<T>::kScaled ? 5 : 4;
+
 template <typename T, bool kWalls>
-__global__ void __launch_bounds__(128) step2_q15_kernel(const StepIO<T> io, const StepArgs a,
+__global__ void __launch_bounds__(128, kQ15Blocks<T>) step2_q15_kernel(const StepIO<T> io, const StepArgs a,
                                                         const PackedRates pr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
@@ -483,9 +491,15 @@ __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const 
     });
 }
 
+// D3Q27 with FP32 storage fits 5 blocks of 128 per SM (at most 96
+// registers) without spills; the others would spill at that bound and run
+// 3 blocks per SM.
+template <int Q, typename T>
+constexpr int kAAOddBlocks = (Q == 27 && !Storage<T>::kScaled) ? 5 : 3;
+
 template <int Q, typename T, bool kWalls>
-__global__ void __launch_bounds__(128) aa_odd_kernel(const StepIO<T> io, const StepArgs a,
-                                                     const PackedRates pr) {
+__global__ void __launch_bounds__(128, (kAAOddBlocks<Q, T>))
+    aa_odd_kernel(const StepIO<T> io, const StepArgs a, const PackedRates pr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
     const int x0 = 2 * t;
