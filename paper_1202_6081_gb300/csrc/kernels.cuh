@@ -491,11 +491,11 @@ __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const 
     });
 }
 
-// D3Q27 with FP32 storage fits 5 blocks of 128 per SM (at most 96
-// registers) without spills; the others would spill at that bound and run
-// 3 blocks per SM.
+// Blocks of 128 per SM, from measurement: D3Q27 at 5 (96 registers; FP32
+// storage without spills, 16-bit with 40 bytes: 38.3k vs 33.3k MLUPS FP16 at
+// 512^3 against 3 blocks); D3Q15 at 4 (24-32 bytes of spills).
 template <int Q, typename T>
-constexpr int kAAOddBlocks = (Q == 27 && !Storage<T>::kScaled) ? 5 : 3;
+constexpr int kAAOddBlocks = Q == 27 ? 5 : 4;
 
 template <int Q, typename T, bool kWalls>
 __global__ void __launch_bounds__(128, (kAAOddBlocks<Q, T>))
