@@ -214,6 +214,29 @@ def test_square_channel_steady_state_vs_series(lbm, Q):
     assert rel_l2(ux, ua) <= 1e-2
 
 
+@pytest.mark.parametrize("Q", [15, 27])
+def test_square_channel_start_matches_oracle(lbm, orc, Q):
+    """The channel workload itself (16 x 64 x 64, walls on y and z,
+    F_x = 1e-6, tau = 0.8, from rest), first 200 steps -- the part the FP64
+    oracle finishes in seconds: relative L2 of u against the oracle within
+    1e-5, in the launch configuration of the 20000-step run (CUDA graphs of
+    32 steps)."""
+    shape = (64, 64, 16)
+    om = W.omegas(Q, 1 / 0.8)
+    F = np.array([1e-6, 0.0, 0.0])
+    S = lbm.Solver(Q, shape, om, force=F, walls=3)
+    S.init_equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    S.step(200)
+    F32 = F.astype(np.float32).astype(np.float64)
+    f_or = orc.run(Q, shape, orc.equilibrium(Q, np.ones(shape), np.zeros((3,) + shape), F32),
+                   F32, om, 200, bc=3)
+    _, u_g = orc.macroscopic(Q, gpu_state(S), F32)
+    _, u_o = orc.macroscopic(Q, f_or, F32)
+    err = rel_l2(u_g, u_o)
+    print("D3Q%d channel, 200 steps: rel L2 u vs oracle %.2e" % (Q, err))
+    assert err <= 1e-5
+
+
 @pytest.mark.parametrize("storage,bound", [("f16", 1e-3), ("bf16", 5e-3)])
 def test_16bit_storage_taylor_green(lbm, orc, storage, bound):
     """D3Q27 Taylor-Green + noise, 32^3, 100 steps, 16-bit storage of
