@@ -182,13 +182,32 @@ def cpu_baseline(size, budget_s=15.0):
     steps, dt = timed(cores, budget_s)
     steps1, dt1 = timed(1, budget_s / 3)
     oracle.run(Q, shape, f, np.zeros(3), om, 0, nthreads=cores)  # restore the thread count
+    # the small configurations, all cores: 32^3 Taylor-Green x 100 steps in
+    # full, and the first 100 steps of the 16 x 64 x 64 channel
+    small = {}
+    for name, Qs, shp, om_s, F, bc, n in (
+            ("D3Q27 32^3 Taylor-Green, 100 steps", 27, (32, 32, 32), W.omegas(27, 1 / 0.6),
+             np.zeros(3), 0, 100),
+            ("D3Q15 16x64x64 channel, first 100 steps", 15, (64, 64, 16), W.omegas(15, 1 / 0.8),
+             np.array([1e-6, 0.0, 0.0]), 3, 100),
+            ("D3Q27 16x64x64 channel, first 100 steps", 27, (64, 64, 16), W.omegas(27, 1 / 0.8),
+             np.array([1e-6, 0.0, 0.0]), 3, 100)):
+        r0, u0 = W.taylor_green(shp, u0=0.02) if bc == 0 else (np.ones(shp),
+                                                             np.zeros((3,) + shp))
+        f0 = oracle.equilibrium(Qs, r0, u0, F)
+        t0 = time.perf_counter()
+        oracle.run(Qs, shp, f0, F, om_s, n, bc=bc, nthreads=cores)
+        t = time.perf_counter() - t0
+        small[name] = {"value": int(np.prod(shp)) * n / t / 1e6, "unit": UNIT,
+                       "seconds": t}
     return {"value": cells * steps / dt / 1e6, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": "%d steps of one %dx%dx%d z-slab of the %d^3 Taylor-Green+noise field "
                       "(periodic), D3Q27, tau=0.6, FP64, %.1f s" % (steps, size, size, nz_s,
                                                                    size, dt),
             "single_thread": {"value": cells * steps1 / dt1 / 1e6, "unit": UNIT, "cores": 1,
-                              "sample": "%d steps of the same slab, %.1f s" % (steps1, dt1)}}
+                              "sample": "%d steps of the same slab, %.1f s" % (steps1, dt1)},
+            "small_configs": small}
 
 
 def run_reference(args):
