@@ -182,3 +182,64 @@ def test_womersley_profiles_match_analytic(lbm, omega_nu, Wo):
         errs.append(np.abs(ux - ua).max() / scale)
     print("Wo %.1f: max error / max |u| over the period: %.2e" % (Wo, max(errs)))
     assert max(errs) <= 1e-2
+
+
+def _duct_steady(lbm, Q, omega_nu, Fx, n=43):
+    shape = (n, n, 3)
+    a = n / 2
+    nu = analytic.viscosity(omega_nu)
+    S = lbm.Solver(Q, shape, W.omegas(Q, omega_nu), force=(Fx, 0.0, 0.0), walls=3)
+    S.init_equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    # slowest mode decays as exp(-2 nu (pi / 2a)^2 t): run to e^-12
+    steps = int(12 / (2 * nu * (np.pi / (2 * a)) ** 2)) + 1
+    S.step(steps)
+    _, u = S.macroscopic()
+    ux = u[0].double().mean(dim=2).cpu().numpy()  # [z, y]
+    c = np.arange(n) + 0.5 - a
+    Z, Y = np.meshgrid(c, c, indexing="ij")
+    ua = analytic.duct_profile(Y, Z, a, Fx, nu)
+    err = np.linalg.norm(ux - ua) / np.linalg.norm(ua)
+    return err, ux.max() * a / nu, steps
+
+
+@pytest.mark.parametrize("Q,omega_nu", [(27, 1.923), (15, 1.818)])
+def test_paper_square_duct_re_65_7(lbm, Q, omega_nu):
+    """Sec. 9 square duct: 3 x 45 x 45 nodes (43 x 43 fluid cells, a = 21.5),
+    centre-line Reynolds number u_max a / nu = 65.7, run to steady state:
+    u_x(y, z) matches the series of Eq. ductFourier within 2e-2 (relative L2)
+    and Re matches 65.7 within 2 % (the coarse grid and tau = 0.52 put the
+    computed profile about 1 % below the series).  D3Q27 runs the stated parameters
+    (F_x = 1e-6, omega_nu = 1.923).  D3Q15 with walls on both y and z is
+    unstable at that omega in this implementation (see the next test), so
+    it runs the same Reynolds number at omega_nu = 1.818 with the force
+    scaled to match (F_x = Re nu / (a u_max(F = 1)))."""
+    a = 43 / 2
+    nu = analytic.viscosity(omega_nu)
+    Fx = 65.7 * nu / (a * analytic.duct_profile(0.0, 0.0, a, 1.0, nu))
+    err, re, steps = _duct_steady(lbm, Q, omega_nu, Fx)
+    print("D3Q%d square duct, omega %.3f, F %.3e, %d steps: rel L2 %.2e, Re %.2f" % (
+        Q, omega_nu, Fx, steps, err, re))
+    assert err <= 2e-2
+    assert re == pytest.approx(65.7, rel=2e-2)
+
+
+def test_d3q15_duct_instability_is_reported(lbm):
+    """D3Q15 with bounce-back walls on both y and z faces at omega_nu = 1.923
+    (the paper's duct parameters) grows a density mode from the duct's
+    corners and overflows within a few thousand steps -- in the FP64 oracle
+    as well (stable up to omega_nu = 1.85, unstable from 1.88; D3Q27 stays
+    stable up to 1.961).  The library reports the overflowed state as
+    LBM_ENONFINITE from the FP64 conservation sums, without any GPU fault,
+    and the context stays usable."""
+    import ctypes
+    n = 43
+    shape = (n, n, 3)
+    S = lbm.Solver(15, shape, W.omegas(15, 1.923), force=(1e-6, 0.0, 0.0), walls=3)
+    S.init_equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    S.step(6000)
+    out = (ctypes.c_double * 4)()
+    assert lbm.load().lbm_conservation(S.ctx, out, None) == 5  # LBM_ENONFINITE
+    S.set_omega(W.omegas(15, 1.818))
+    S.init_equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    S.step(3000)
+    assert np.isfinite(S.conservation()).all()
