@@ -209,10 +209,10 @@ def test_paper_square_duct_re_65_7(lbm, Q, omega_nu):
     u_x(y, z) matches the series of Eq. ductFourier within 2e-2 (relative L2)
     and Re matches 65.7 within 2 % (the coarse grid and tau = 0.52 put the
     computed profile about 1 % below the series).  D3Q27 runs the stated parameters
-    (F_x = 1e-6, omega_nu = 1.923).  D3Q15 with walls on both y and z is
-    unstable at that omega in this implementation (see the next test), so
-    it runs the same Reynolds number at omega_nu = 1.818 with the force
-    scaled to match (F_x = Re nu / (a u_max(F = 1)))."""
+    (F_x = 1e-6, omega_nu = 1.923).  D3Q15 is unstable at that omega for a
+    flow in the y-z plane (see the next test), so it runs the same Reynolds
+    number at omega_nu = 1.818 with the force scaled to match
+    (F_x = Re nu / (a u_max(F = 1)))."""
     a = 43 / 2
     nu = analytic.viscosity(omega_nu)
     Fx = 65.7 * nu / (a * analytic.duct_profile(0.0, 0.0, a, 1.0, nu))
@@ -224,11 +224,11 @@ def test_paper_square_duct_re_65_7(lbm, Q, omega_nu):
 
 
 def test_d3q15_duct_instability_is_reported(lbm):
-    """D3Q15 with bounce-back walls on both y and z faces at omega_nu = 1.923
-    (the paper's duct parameters) grows a density mode from the duct's
-    corners and overflows within a few thousand steps -- in the FP64 oracle
-    as well (stable up to omega_nu = 1.85, unstable from 1.88; D3Q27 stays
-    stable up to 1.961).  The library reports the overflowed state as
+    """D3Q15 on the duct at omega_nu = 1.923 (the paper's parameters) grows a
+    density mode and overflows within a few thousand steps -- in the FP64
+    oracle as well (stable up to omega_nu = 1.85, unstable from 1.88; any
+    flow in the y-z plane does this, the walls are not the cause; D3Q27
+    stays stable up to 1.961).  The library reports the overflowed state as
     LBM_ENONFINITE from the FP64 conservation sums, without any GPU fault,
     and the context stays usable."""
     import ctypes
