@@ -105,7 +105,6 @@ struct Storage<float> {
     static constexpr bool kScaled = false;
     __device__ __forceinline__ static float load(const float *p) { return __ldg(p); }
     __device__ __forceinline__ static void store(float *p, float v) { __stcs(p, v); }
-    __device__ __forceinline__ static float from_f(float v) { return v; }
 };
 
 template <>
@@ -187,14 +186,7 @@ __device__ __forceinline__ unsigned pack_sr(float lo, float hi, unsigned salt) {
     return PackSR<T>::run(lo, hi, sr_bits<q>(lo, hi, salt));
 }
 
-// Stored value -> deviation f - w (FP32), and back.
-template <int Q, typename T>
-__device__ __forceinline__ float load_dev(const T *p, int a) {
-    const float v = Storage<T>::load(p);
-    if (Storage<T>::kScaled) return v * float(weight<Q>(a));
-    return v;
-}
-
+// Deviation f - w (FP32) -> stored value.
 template <int Q, typename T>
 __device__ __forceinline__ void store_dev(T *p, int a, float dev) {
     if (Storage<T>::kScaled)
@@ -299,14 +291,6 @@ __device__ __forceinline__ void gather(const T *__restrict__ fin, const Grid &g,
         // the weight of a slot and of its opposite are equal
         f[a] = Storage<T>::kScaled ? v * float(weight<Q>(a)) : v;
     }
-}
-
-// Store post-collision deviations of one cell at its own position.
-template <int Q, typename T>
-__device__ __forceinline__ void store_own(T *__restrict__ fout, const Grid &g, long long own,
-                                          const float (&f)[Q]) {
-#pragma unroll
-    for (int a = 0; a < Q; ++a) store_dev<Q, T>(fout + (long long)a * g.pop + own, a, f[a]);
 }
 
 // Inverse of the pull: place the pre-collision values f_alpha(x) of one cell
