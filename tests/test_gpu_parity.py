@@ -76,6 +76,34 @@ def test_one_step_from_random_state(lbm, orc, Q, bc, shape):
     assert np.abs(got - want).max() <= 2e-6
 
 
+DEGENERATE = [(1, 1, 1), (1, 1, 2), (2, 1, 6), (1, 5, 4), (3, 2, 1)]  # (nz, ny, nx)
+
+
+@pytest.mark.parametrize("Q", [27, 15])
+@pytest.mark.parametrize("bc", [0, 3])
+@pytest.mark.parametrize("shape", DEGENERATE)
+def test_degenerate_grids_match_oracle(lbm, orc, Q, bc, shape):
+    """Grids one cell thick (a cell is its own neighbour, or, with walls,
+    bounces off both faces at once) and single-cell grids: 7 steps from a
+    perturbed equilibrium with a uniform force against the oracle, in both
+    streaming schemes where nx is even; zero steps leave the state
+    untouched."""
+    rng = W.rng(130 + bc)
+    rho = 1.0 + rng.uniform(-0.01, 0.01, shape)
+    u = rng.uniform(-0.05, 0.05, (3,) + shape)
+    F = np.array([2e-4, -1e-4, 1e-4])
+    f0 = orc.equilibrium(Q, rho, u, F) + rng.uniform(-1e-3, 1e-3, (Q,) + shape)
+    om = W.omegas(Q, 1.6)
+    want = orc.run(Q, shape, f0, F, om, 7, bc=bc)
+    for inplace in ([False, True] if shape[2] % 2 == 0 else [False]):
+        S = lbm.Solver(Q, shape, om, force=F, walls=bc, inplace=inplace)
+        S.set_state(f0)
+        S.step(0)
+        assert np.abs(gpu_state(S) - f0).max() <= 1e-7  # FP32 storage of f0
+        S.step(7)
+        assert np.abs(gpu_state(S) - want).max() <= 2e-6, inplace
+
+
 @pytest.mark.parametrize("Q", [27, 15])
 @pytest.mark.parametrize("shape", [(6, 11, 35), (6, 11, 36)])  # one-cell and two-cell kernels
 def test_one_step_with_force_field(lbm, orc, Q, shape):
