@@ -21,8 +21,15 @@
  *     matrix of App. G for D3Q15).
  *   - Dense fields exchanged with the caller are structure-of-arrays:
  *     distributions [Q][nz][ny][nx], vectors [3][nz][ny][nx], scalars
- *     [nz][ny][nx].  Every pointer argument named "device" is device memory
- *     of the GPU that was current at lbm_create; "host" is host memory.
+ *     [nz][ny][nx].  Every pointer argument named "device" is memory the
+ *     GPU that was current at lbm_create addresses directly: its own device
+ *     memory, or page-locked host memory mapped into its address space
+ *     (cudaHostAlloc / cudaHostRegister under unified addressing).  The
+ *     dense fields of lbm_init_equilibrium, lbm_set_state, lbm_get_state
+ *     and lbm_macroscopic may be such host buffers: the kernels then read
+ *     or write them across the host link themselves, with no separate copy
+ *     (state buffers, force fields and adjoint fields must be device
+ *     memory).  "host" is plain host memory.
  *   - Ownership: the caller allocates and frees every device buffer and owns
  *     every stream.  The library allocates only its context and a small
  *     reduction scratch, both released by lbm_destroy.

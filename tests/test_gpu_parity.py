@@ -440,3 +440,30 @@ def test_calls_out_of_order_and_non_finite_state_are_reported(lbm):
     finally:
         torch.cuda.synchronize()
         lbm.lbm_destroy(ctx)
+
+
+def test_host_mapped_fields_equal_device_fields(lbm):
+    """Dense fields in page-locked host memory (read and written by the
+    kernels across the host link) give results identical to device fields:
+    init from host rho, u; state and macroscopic fields back into host."""
+    Q = 27
+    shape = (5, 6, 8)
+    rho, u = W.taylor_green(shape, u0=0.03, noise=1e-2, seed=141)
+    om = W.omegas(Q, 1.5)
+    h_rho = torch.from_numpy(rho).pin_memory()
+    h_u = torch.from_numpy(u).pin_memory()
+    A = lbm.Solver(Q, shape, om, force=(1e-4, 0.0, 0.0))
+    B = lbm.Solver(Q, shape, om, force=(1e-4, 0.0, 0.0))
+    A.init_equilibrium(rho, u)
+    lbm.lbm_init_equilibrium(B.ctx, h_rho, h_u)
+    A.step(5)
+    B.step(5)
+    ra, ua = A.macroscopic()
+    hr = torch.empty(shape, dtype=torch.float32).pin_memory()
+    hu = torch.empty((3,) + shape, dtype=torch.float32).pin_memory()
+    hf = torch.empty((Q,) + shape, dtype=torch.float64).pin_memory()
+    lbm.lbm_macroscopic(B.ctx, hr, hu)
+    lbm.lbm_get_state(B.ctx, hf)
+    torch.cuda.synchronize()
+    assert torch.equal(ra.cpu(), hr) and torch.equal(ua.cpu(), hu)
+    assert torch.equal(A.get_state().cpu(), hf)
