@@ -31,11 +31,12 @@
  *     (state buffers, force fields and adjoint fields must be device
  *     memory).  "host" is plain host memory.
  *   - Ownership: the caller allocates and frees every device buffer and owns
- *     every stream.  The library allocates only its context and a small
- *     reduction scratch, both released by lbm_destroy.
+ *     every stream it passes.  The library allocates only its context, a
+ *     small reduction scratch, and for lbm_step a private capture stream and
+ *     the CUDA graphs it captures, all released by lbm_destroy.
  *   - Streams: a `void *stream` argument is a cudaStream_t (NULL = the legacy
  *     default stream).  Every call is asynchronous on that stream except
- *     lbm_conservation, which synchronises it.
+ *     lbm_conservation and lbm_kinetic_energy, which synchronise it.
  *   - Errors: every call returns an lbm_status; nothing throws, aborts or
  *     prints.  Argument errors are detected before any work is enqueued and
  *     leave the context unchanged.  A CUDA launch error is reported as
@@ -58,7 +59,10 @@ typedef enum { LBM_D3Q15 = 15, LBM_D3Q27 = 27 } lbm_lattice;
 /* How the two state buffers hold the distributions.  All arithmetic is FP32
  * whatever the storage.  LBM_STORE_F32 keeps f - w_a (the deviation from the
  * lattice weight w_a, the rest state at rho = 1) in FP32; the 16-bit modes
- * keep (f - w_a) / w_a rounded to nearest-even in FP16 or BF16. */
+ * keep (f - w_a) / w_a in FP16 or BF16, stochastically rounded by the step
+ * (up or down with probability proportional to the distance, from bits
+ * hashed out of the values and the cell, so a recomputed step rounds the
+ * same way) and rounded to nearest when a state is loaded. */
 typedef enum { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2 } lbm_storage;
 
 typedef enum {
@@ -116,8 +120,9 @@ lbm_status lbm_create(lbm_lattice lattice, int nx, int ny, int nz, const double 
                       const double *force, unsigned bc_flags, lbm_storage storage,
                       lbm_ctx **out);
 
-/* Release the context and its reduction scratch (not the caller's buffers).
- * Safe on NULL.  Work already enqueued must have completed. */
+/* Release the context, its reduction scratch, capture stream and CUDA
+ * graphs (not the caller's buffers).  Safe on NULL.  Work already enqueued
+ * must have completed. */
 void lbm_destroy(lbm_ctx *ctx);
 
 /* Size in bytes of each of the two state buffers the caller must provide:
