@@ -248,7 +248,7 @@ def test_d3q15_duct_instability_is_reported(lbm):
 @pytest.mark.parametrize("Q", [27, 15])
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_taylor_green_2d_decay_matches_closed_form(lbm, Q, storage):
-    """z-invariant 2D Taylor-Green vortex (the C1 flow's closed form) at
+    """z-invariant 2D Taylor-Green vortex (the closed-form case of the 32^3 flow) at
     128^2, omega_nu = 1.9 (nu = 0.0088), beyond the oracle's reach: between
     steps 500 and 2500 the kinetic energy decays at 2 nu (kx^2 + ky^2)
     within 2.5e-3 (the O(k^2) lattice error is -1.2e-3), for FP32 and
