@@ -73,3 +73,28 @@ def test_null_context_calls_are_safe(lib):
     assert lib.lbm_conservation(None, None, None) == 1
     assert lib.lbm_status_string(0).decode() == "LBM_OK"
     assert "EINVAL" in lib.lbm_status_string(1).decode()
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without liblbm.so the binding raises instead of
+    computing anything another way."""
+    from paper_1202_6081_gb300 import lbm
+    monkeypatch.setattr(lbm, "_lib", None)
+    monkeypatch.setattr(lbm, "LIB_PATH", str(tmp_path / "liblbm.so"))
+    with pytest.raises(RuntimeError, match="liblbm.so not found"):
+        lbm.load()
+    with pytest.raises(RuntimeError):
+        lbm.lbm_create(27, 4, 4, 4, [1.0] * 27)
+
+
+def test_no_gpu_fails_loudly(lib):
+    """Without a usable GPU, creating a context reports LBM_ECUDA (or the
+    Solver raises before that); nothing runs on the CPU instead."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1202_6081_gb300 import lbm
+    with pytest.raises(Exception):
+        lbm.lbm_create(27, 4, 4, 4, [1.0] * 27)
+    with pytest.raises(Exception):
+        lbm.Solver(27, (4, 4, 4), [1.0] * 27)
