@@ -531,7 +531,14 @@ def run_ours(args):
 def main():
     args = parse()
     if args.impl == "reference":
-        return run_reference(args)
+        try:
+            return run_reference(args)
+        except Exception as e:  # the oracle could not be built or run here
+            if dist_env()[0] == 0:
+                print(json.dumps({"impl": "reference",
+                                  "unavailable": "FP64 oracle failed: %s" % str(e)[:200]}),
+                      flush=True)
+            return 0
     return run_ours(args)
 
 
