@@ -67,3 +67,41 @@ def test_random_configuration_matches_oracle(lbm, orc, i):
     want = orc.run(Q, shape, f0, F, om, steps, bc=bc)
     err = np.abs(got - want).max()
     assert err <= 3e-6, (Q, shape, bc, inplace, field, steps, graph_steps, omega_nu, err)
+
+
+@pytest.mark.parametrize("i", range(20))
+def test_random_adjoint_configuration_matches_oracle(lbm, orc, i):
+    """The D3Q27 adjoint step (one-cell or two-cell kernel by the parity of
+    nx) and the kinetic-energy seed on random grids, walls, storage types and
+    forces, against the oracle's complex-step adjoint."""
+    rng = W.rng(9500 + i)
+    Q = 27
+    shape = (int(rng.integers(1, 9)), int(rng.integers(1, 9)), int(rng.integers(1, 25)))
+    bc = int(rng.integers(0, 4))
+    storage = str(rng.choice(["f32", "f16", "bf16"]))
+    field = bool(rng.integers(0, 2))
+    F = (rng.uniform(-1e-3, 1e-3, (3,) + shape) if field else rng.uniform(-1e-3, 1e-3, 3))
+    F = F.astype(np.float32).astype(np.float64)
+    rho = 1.0 + rng.uniform(-0.01, 0.01, shape)
+    u = rng.uniform(-0.05, 0.05, (3,) + shape)
+    om = W.random_omegas(Q, seed=9600 + i)
+    S = lbm.Solver(Q, shape, om, force=F, walls=bc, storage=storage)
+    S.init_equilibrium(rho, u)
+    f_t = S.get_state().cpu().numpy()  # the stored state, as the kernels read it
+    lam_next = rng.standard_normal((Q,) + shape)
+    ln = S.new_adjoint_field()
+    S.adjoint_view(ln).copy_(torch.as_tensor(lam_next, dtype=torch.float32))
+    lo = S.new_adjoint_field()
+    gF = torch.zeros((3,) + shape, dtype=torch.float32, device="cuda")
+    S.adjoint_step(S.current_buffer(), ln, lo, gF)
+    seed = S.new_adjoint_field()
+    S.kinetic_energy_seed(S.current_buffer(), seed)
+    torch.cuda.synchronize()
+    gF_want = np.zeros((3,) + shape)
+    want = orc.adjoint_step(Q, shape, f_t, F, om, lam_next, bc=bc, gF=gF_want)
+    got = S.adjoint_view(lo).cpu().numpy()
+    cfg = (shape, bc, storage, field)
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max(), cfg
+    assert np.abs(gF.cpu().numpy() - gF_want).max() <= 1e-5 * np.abs(gF_want).max(), cfg
+    seed_want, _ = orc.kinetic_energy_grad(Q, f_t, F)
+    assert np.abs(S.adjoint_view(seed).cpu().numpy() - seed_want).max() <= 1e-6, cfg
