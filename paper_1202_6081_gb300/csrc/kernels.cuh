@@ -204,7 +204,8 @@ struct Pair<__nv_bfloat16> : Pair16<__nv_bfloat16> {
 };
 
 // Relaxation rates pre-broadcast to both lanes, built on the host:
-// D3Q27 omega, -omega, 1 - omega; D3Q15 omega / k_beta.
+// D3Q27 omega, -omega, 1 - omega (divided by 216 for the kernels that fold
+// the weights of 16-bit storage into their sums); D3Q15 omega / k_beta.
 struct PackedRates {
     unsigned long long w[27], nw[27], omw[27];
     unsigned long long w15[15];
