@@ -109,6 +109,14 @@ __global__ void __launch_bounds__(128, 3) adjoint2_kernel(const StepIO<T> io, co
         Fy = f2(a.F[1]);
         Fz = f2(a.F[2]);
     }
+    // the dJ/dF accumulator is read now, so its latency hides behind the
+    // collision's reverse; it is written back at the end
+    f2 a0 = f2(0.0f), a1 = f2(0.0f), a2 = f2(0.0f);
+    if (g.gF) {
+        a0 = f2(g.gF[c], g.gF[c + 1]);
+        a1 = f2(g.gF[N + c], g.gF[N + c + 1]);
+        a2 = f2(g.gF[2 * N + c], g.gF[2 * N + c + 1]);
+    }
     const Rates27<f2> r = load_rates_packed(pr);
     f2 lam[27], gx, gy, gz;
     adjoint27<f2>(f, Fx, Fy, Fz, r, mu, lam, gx, gy, gz);
@@ -117,12 +125,15 @@ __global__ void __launch_bounds__(128, 3) adjoint2_kernel(const StepIO<T> io, co
         Pair<float>::st2(g.lam_out[q] + own, lam[q]);
     });
     if (g.gF) {
-        g.gF[c] += gx.lo();
-        g.gF[c + 1] += gx.hi();
-        g.gF[N + c] += gy.lo();
-        g.gF[N + c + 1] += gy.hi();
-        g.gF[2 * N + c] += gz.lo();
-        g.gF[2 * N + c + 1] += gz.hi();
+        a0 = a0 + gx;
+        a1 = a1 + gy;
+        a2 = a2 + gz;
+        g.gF[c] = a0.lo();
+        g.gF[c + 1] = a0.hi();
+        g.gF[N + c] = a1.lo();
+        g.gF[N + c + 1] = a1.hi();
+        g.gF[2 * N + c] = a2.lo();
+        g.gF[2 * N + c + 1] = a2.hi();
     }
 }
 
