@@ -79,9 +79,12 @@ def _backward_segments(S, nsteps, every, ckpts, seed, gF):
         t0 = s * every
         t1 = min(t0 + every, nsteps)
         ring[0].copy_(ckpts[s])
-        for i in range(t1 - t0):
+        # the adjoint steps need the states t0 .. t1 - 1; the state at t1 is
+        # recomputed only in the last segment, where it seeds the adjoint
+        last = s == nseg - 1
+        for i in range(t1 - t0 if last else t1 - t0 - 1):
             S.step_into(ring[i], ring[i + 1])
-        if s == nseg - 1:
+        if last:
             seed(ring[t1 - t0], lam)
         for i in reversed(range(t1 - t0)):
             S.adjoint_step(ring[i], lam, lam2, gF)
