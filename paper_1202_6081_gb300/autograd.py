@@ -59,10 +59,16 @@ def _check_force(F):
 
 
 def _forward_with_checkpoints(solver, nsteps, every):
+    """nsteps steps in runs of `every` (one library call per run, so long
+    runs go out as CUDA graphs), with a copy of the state at the start of
+    each run."""
     ckpts = [solver.current_buffer().clone()]
-    for t in range(nsteps):
-        solver.step(1)
-        if (t + 1) % every == 0 and t + 1 < nsteps:
+    done = 0
+    while done < nsteps:
+        n = min(every, nsteps - done)
+        solver.step(n)
+        done += n
+        if done < nsteps:
             ckpts.append(solver.current_buffer().clone())
     return ckpts
 
