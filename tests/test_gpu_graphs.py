@@ -60,3 +60,30 @@ def test_graph_steps_argument_checks(lbm):
         assert lib.lbm_set_graph_steps(ctx, 64) == 0
     finally:
         lbm.lbm_destroy(ctx)
+
+
+def test_steps_inside_a_callers_graph_capture(lbm):
+    """lbm_step called while the caller captures its stream into a CUDA
+    graph (torch.cuda.graph): the library sees the capture and launches each
+    step on its own, so the caller's graph holds the steps; replaying it
+    advances the state exactly like direct calls."""
+    Q = 27
+    shape = (4, 6, 10)
+    rho, u = W.taylor_green(shape, u0=0.03, noise=1e-2, seed=71)
+    om = W.omegas(Q, 1.4)
+    ref = lbm.Solver(Q, shape, om, force=(1e-4, 0.0, 0.0))
+    cap = lbm.Solver(Q, shape, om, force=(1e-4, 0.0, 0.0))
+    ref.init_equilibrium(rho, u)
+    cap.init_equilibrium(rho, u)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            cap.step(4, stream=s)  # an even count: the captured run returns to its parity
+    torch.cuda.synchronize()
+    for _ in range(5):
+        g.replay()
+    ref.step(20)
+    torch.cuda.synchronize()
+    assert torch.equal(ref.get_state(), cap.get_state())
