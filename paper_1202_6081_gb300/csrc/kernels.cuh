@@ -1,6 +1,7 @@
 // Kernels of liblbm.so, templated over the lattice (Q = 27 or 15) and the
-// storage type (float, __half, __nv_bfloat16).  kernels_q27.cu and
-// kernels_q15.cu instantiate them; api.cu calls the launchers.
+// storage type (float, __half, __nv_bfloat16).  kernels_q27_f32.cu,
+// kernels_q27_f16.cu, kernels_q27_bf16.cu and kernels_q15.cu instantiate
+// them; api.cu calls the launchers.
 #pragma once
 
 #include "collide_q15.cuh"
@@ -679,8 +680,9 @@ __global__ void __launch_bounds__(kRedThreads) conservation_kernel(const T *__re
         for (int k = 0; k < 4; ++k) part[4 * blockIdx.x + k] = sh[k][0];
 }
 
-// Launchers.  kernels_q27.cu / kernels_q15.cu hold their explicit
-// instantiations; api.cu sees them through the extern declarations below.
+// Launchers.  The kernels_q27_*.cu and kernels_q15.cu units hold their
+// explicit instantiations; api.cu sees them through the extern declarations
+// below.
 inline unsigned long long splat_bits(float v) {
     unsigned int u;
     memcpy(&u, &v, 4);
@@ -705,8 +707,8 @@ inline PackedRates packed_rates(const StepArgs &a, bool weighted = false) {
     return p;
 }
 
-// The packed two-cells-per-thread kernel serves D3Q27 grids with even nx;
-// every other grid takes the one-cell kernel.
+// The two-cells-per-thread kernels serve grids with even nx (D3Q27 and
+// D3Q15); odd nx takes the one-cell kernel.
 template <int Q, typename T>
 cudaError_t launch_step(const void *fin, void *fout, const StepArgs &a, cudaStream_t st) {
     StepIO<T> io;
