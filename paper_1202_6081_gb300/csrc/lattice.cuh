@@ -133,11 +133,12 @@ struct Storage<__nv_bfloat16> {
 // ------------------------------------------------- stochastic 16-bit rounding
 // The step stores 16-bit values with stochastic rounding: up or down with
 // probability proportional to the distance, so each stored value is exact
-// in expectation.  Round-to-nearest of a smooth field gives a rounding error
-// that is itself a smooth function of position wherever the field is flat,
-// and that coherent error is re-made identically every step and accumulates
-// (FP16 storage of the 512^3 Taylor-Green flow drifts to 1.5e-3 relative
-// error of u in 500 steps that way).  The conversions are sm_100-class
+// in expectation.  Round-to-nearest re-makes the rounding error of a slowly
+// varying value with the same sign step after step, coherently over a
+// smooth field, and that error accumulates (FP16 storage of the 512^3
+// Taylor-Green flow drifts to 1.5e-3 relative error of u in 500 steps that
+// way; a dither fixed per cell drifts the same way, so the random bits must
+// change as the values do).  The conversions are sm_100-class
 // cvt.rs.{f16x2,bf16x2}.f32, fed 32 random bits.  The bits are a hash of the
 // two values being rounded, of the cell pair's position and of the
 // population, so the rounding is a fixed function of the state: a step
