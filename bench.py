@@ -328,13 +328,15 @@ def e2e_job(torch, lbm, size, steps):
                    "rho,u (FP32) written by the macroscopic kernel to pinned host memory" % steps}
 
 
-def adjoint_timing(torch, lbm, size, steps=100):
-    """Adjoint step vs forward step at the adjoint workload (D3Q27, size^3
-    periodic, tau = 0.6, per-cell force field), both by CUDA events; plus a
-    whole checkpointed gradient (200 steps, checkpoint every 20)."""
+def adjoint_timing(torch, lbm, size, steps=100, Q=27):
+    """Adjoint step vs forward step at the adjoint workload (D3Q27 or D3Q15,
+    size^3 periodic, tau = 0.6, per-cell force field), both by CUDA events;
+    plus a whole checkpointed gradient (200 steps, checkpoint every 20).
+    Algorithmic bytes of an adjoint step per cell: f_t, lam_{t+1} read and
+    lam_t written (3 Q x 4 B), the force field read and dJ/dF read and
+    written (36 B)."""
     import workloads as W
     from paper_1202_6081_gb300.autograd import kinetic_energy_after
-    Q = 27
     shape = (size, size, size)
     om = W.omegas(Q, 1 / 0.6)
     rho, u = W.taylor_green(shape, u0=0.02, noise=1e-3)
@@ -376,10 +378,10 @@ def adjoint_timing(torch, lbm, size, steps=100):
     J.backward()
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    return {"workload": "D3Q27 %d^3 periodic, tau=0.6, force field, FP32" % size,
+    return {"workload": "D3Q%d %d^3 periodic, tau=0.6, force field, FP32" % (Q, size),
             "forward_ms_per_step": t_fwd * 1e3, "adjoint_ms_per_step": t_adj * 1e3,
             "adjoint_forward_ratio": t_adj / t_fwd,
-            "adjoint_GB/s": 360 * cells / t_adj / 1e9,
+            "adjoint_GB/s": (12 * Q + 36) * cells / t_adj / 1e9,
             "gradient_200_steps": {"forward_s": t1 - t0, "backward_s": t2 - t1,
                                    "backward_forward_ratio": (t2 - t1) / (t1 - t0)}}
 
@@ -437,8 +439,8 @@ def run_ours(args):
     size = args.size
     if args.adjoint_only:
         if rank == 0:
-            print(json.dumps({"adjoint": adjoint_timing(torch, lbm, size, steps=args.steps)}),
-                  flush=True)
+            print(json.dumps({"adjoint": adjoint_timing(torch, lbm, size, steps=args.steps,
+                                                        Q=args.lattice)}), flush=True)
         return 0
     lat, st = args.lattice, args.storage
     S, _, _ = make_solver(lbm, lat, size, st, 0.6, inplace=args.inplace)
@@ -518,6 +520,7 @@ def run_ours(args):
         result["inplace_aa"] = aa
         result["small_grids"] = small_grids(torch, lbm)
         result["adjoint"] = adjoint_timing(torch, lbm, 128)
+        result["adjoint_q15"] = adjoint_timing(torch, lbm, 128, Q=15)
         torch.cuda.empty_cache()
         result["cpu_baseline"] = cpu_baseline(size)
     if rank == 0:

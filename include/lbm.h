@@ -202,8 +202,8 @@ lbm_status lbm_macroscopic(const lbm_ctx *ctx, float *rho, float *u, void *strea
  * still written). */
 lbm_status lbm_conservation(lbm_ctx *ctx, double out[4], void *stream);
 
-/* ---- discrete adjoint (D3Q27; not in the paper: the reverse mode of its
- * update, for gradients with respect to a per-cell body force) ---------- */
+/* ---- discrete adjoint (D3Q27 and D3Q15; not in the paper: the reverse mode
+ * of its update, for gradients with respect to a per-cell body force) --- */
 
 /* Size in bytes of one adjoint field lam: FP32, laid out like an FP32 state
  * buffer (Q population planes of pitched rows; see lbm_state_bytes). */
@@ -230,7 +230,7 @@ lbm_status lbm_step_into(lbm_ctx *ctx, const void *f_in, void *f_out, void *stre
  * (device FP32 [3][nz][ny][nx], accumulated; the force of step t is the
  * bound force field or the uniform force).  lam_next, lam_out: device FP32
  * adjoint fields (lbm_adjoint_bytes, 16-byte aligned, distinct).
- * Errors: LBM_EINVAL, LBM_EUNSUPPORTED (D3Q15, LBM_INPLACE), LBM_ECUDA. */
+ * Errors: LBM_EINVAL, LBM_EUNSUPPORTED (LBM_INPLACE context), LBM_ECUDA. */
 lbm_status lbm_adjoint_step(lbm_ctx *ctx, const void *f_t, const float *lam_next,
                             float *lam_out, float *dJdF, void *stream);
 
@@ -243,8 +243,7 @@ lbm_status lbm_kinetic_energy(lbm_ctx *ctx, const void *f, double *out, void *st
 
 /* Seed of the adjoint of J: lam_out = dJ/df of the state in f (NULL =
  * current), lam_a = u.e_a - |u|^2/2, and, when dJdF is not NULL, the direct
- * term dJdF += u/2.  Errors: LBM_EINVAL, LBM_ESTATE, LBM_EUNSUPPORTED (D3Q15),
- * LBM_ECUDA. */
+ * term dJdF += u/2.  Errors: LBM_EINVAL, LBM_ESTATE, LBM_ECUDA. */
 lbm_status lbm_kinetic_energy_seed(lbm_ctx *ctx, const void *f, float *lam_out, float *dJdF,
                                    void *stream);
 
@@ -259,7 +258,7 @@ lbm_status lbm_kinetic_energy_seed(lbm_ctx *ctx, const void *f, float *lam_out, 
  * and, when dJdF is not NULL, the direct term dJdF_i += g_u_i / (2 rho).
  * lam_out: an adjoint field (lbm_adjoint_bytes, 16-byte aligned).  Not in
  * the paper (reverse mode of its output step).
- * Errors: LBM_EINVAL, LBM_ESTATE, LBM_EUNSUPPORTED (D3Q15), LBM_ECUDA. */
+ * Errors: LBM_EINVAL, LBM_ESTATE, LBM_ECUDA. */
 lbm_status lbm_macroscopic_seed(lbm_ctx *ctx, const void *f, const float *g_rho,
                                 const float *g_u, float *lam_out, float *dJdF, void *stream);
 

@@ -19,7 +19,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels_q27_f32.cu", "kernels_q27_f16.cu", "kernels_q27_bf16.cu", "kernels_q15.cu", "api.cu"]
+SOURCES = ["kernels_q27_f32.cu", "kernels_q27_f16.cu", "kernels_q27_bf16.cu", "kernels_q15.cu",
+           "kernels_q15_adjoint.cu", "api.cu"]
 
 
 def nvcc() -> str:

@@ -1,5 +1,5 @@
-// Kernels of the discrete adjoint of the D3Q27 step and of the kinetic-energy
-// objective (not in the paper: the reverse mode of its update).
+// Kernels of the discrete adjoint of the step (D3Q27 and D3Q15) and of the
+// seeds of the objectives (not in the paper: the reverse mode of its update).
 //
 // Forward step (pull form): f_{t+1}[a](x) = C_a(f_t(x - e_a)), or, behind a
 // bounce-back wall, C_opp(a)(f_t(x)).  Its transpose for the adjoint
@@ -11,38 +11,74 @@
 // pitched rows).
 #pragma once
 
+#include "adjoint_q15.cuh"
 #include "adjoint_q27.cuh"
 #include "kernels.cuh"
 
 namespace lbm {
 
+// Per-cell reverse of the collision, chosen by the lattice (array size).
+template <typename V>
+__device__ __forceinline__ void adjoint_collide(const V (&f)[27], V Fx, V Fy, V Fz,
+                                                const Rates27<V> &r, const V (&mu)[27],
+                                                V (&lam)[27], V &gx, V &gy, V &gz) {
+    adjoint27<V>(f, Fx, Fy, Fz, r, mu, lam, gx, gy, gz);
+}
+template <typename V>
+__device__ __forceinline__ void adjoint_collide(const V (&f)[15], V Fx, V Fy, V Fz,
+                                                const Rates15<V> &r, const V (&mu)[15],
+                                                V (&lam)[15], V &gx, V &gy, V &gz) {
+    adjoint15<V>(f, Fx, Fy, Fz, r, mu, lam, gx, gy, gz);
+}
+
+// The rates of lattice Q in both lanes, from the host-built PackedRates.
+template <int Q>
+struct PairRates;
+template <>
+struct PairRates<27> {
+    using type = Rates27<f2>;
+    static __device__ __forceinline__ type load(const PackedRates &p) {
+        return load_rates_packed(p);
+    }
+};
+template <>
+struct PairRates<15> {
+    using type = Rates15<f2>;
+    static __device__ __forceinline__ type load(const PackedRates &p) {
+        Rates15<f2> r;
+#pragma unroll
+        for (int b = 0; b < 15; ++b) r.w[b] = f2(p.w15[b]);
+        return r;
+    }
+};
+
 struct AdjointArgs {
-    const float *lam_next[27];  // planes of lam_{t+1}
+    const float *lam_next[27];  // planes of lam_{t+1} (the first Q used)
     float *lam_out[27];         // planes of lam_t
     float *gF;                  // dense [3][N] accumulator or nullptr
 };
 
-template <typename T, bool kWalls>
+template <int Q, typename T, bool kWalls>
 __global__ void __launch_bounds__(128) adjoint_kernel(const StepIO<T> io, const AdjointArgs g,
                                                       const StepArgs a) {
     int x, y, z;
     if (!cell_coords(a.g, x, y, z)) return;
     const Rows<kWalls> R = pull_rows<kWalls>(a.g, y, z);
     const int xs[3] = {(x + 1 == a.g.nx) ? 0 : x + 1, x, (x == 0) ? a.g.nx - 1 : x - 1};
-    float f[27], mu[27];
+    float f[Q], mu[Q];
 #pragma unroll
-    for (int q = 0; q < 27; ++q) {
-        const int i = ex<27>(q) + 1, j = ey<27>(q) + 1, k = ez<27>(q) + 1;
+    for (int q = 0; q < Q; ++q) {
+        const int i = ex<Q>(q) + 1, j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
         // state at t: pull from x - e_q
         float v;
         if (kWalls && R.wall[j][k])
-            v = Storage<T>::load(io.in[opposite<27>(q)] + R.own + x);
+            v = Storage<T>::load(io.in[opposite<Q>(q)] + R.own + x);
         else
             v = Storage<T>::load(io.in[q] + R.off[j][k] + xs[i]);
-        f[q] = Storage<T>::kScaled ? v * float(weight<27>(q)) : v;
+        f[q] = Storage<T>::kScaled ? v * float(weight<Q>(q)) : v;
         // adjoint at t+1: from x + e_q (the mirrored pull)
         if (kWalls && R.wall[2 - j][2 - k])
-            mu[q] = __ldg(g.lam_next[opposite<27>(q)] + R.own + x);
+            mu[q] = __ldg(g.lam_next[opposite<Q>(q)] + R.own + x);
         else
             mu[q] = __ldg(g.lam_next[q] + R.off[2 - j][2 - k] + xs[2 - i]);
     }
@@ -50,11 +86,11 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const StepIO<T> io, const 
     const long long c = dense_index(a.g, x, y, z);
     float Fx, Fy, Fz;
     cell_force(a, c, N, Fx, Fy, Fz);
-    const Rates27<float> r = load_rates27(a);
-    float lam[27], gx, gy, gz;
-    adjoint27(f, Fx, Fy, Fz, r, mu, lam, gx, gy, gz);
+    const typename Rates<Q>::type r = load_rates<Q>(a);
+    float lam[Q], gx, gy, gz;
+    adjoint_collide<float>(f, Fx, Fy, Fz, r, mu, lam, gx, gy, gz);
 #pragma unroll
-    for (int q = 0; q < 27; ++q) __stcs(g.lam_out[q] + R.own + x, lam[q]);
+    for (int q = 0; q < Q; ++q) __stcs(g.lam_out[q] + R.own + x, lam[q]);
     if (g.gF) {
         g.gF[c] += gx;
         g.gF[N + c] += gy;
@@ -67,7 +103,10 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const StepIO<T> io, const 
 // the adjoint is pulled from the mirrored neighbours x + e_q: for e_x = 0 an
 // aligned pair, for e_x = +1 the cells (x0 + 1, x0 + 2), for e_x = -1
 // (x0 - 1, x0).
-template <typename T, bool kWalls>
+// 3 blocks of 128 threads per SM: 168 registers.  D3Q27 spills a few of its
+// 242 there but beats 2 blocks; D3Q15 fits without spills (4 blocks would
+// spill 276 B).
+template <int Q, typename T, bool kWalls>
 __global__ void __launch_bounds__(128, 3) adjoint2_kernel(const StepIO<T> io, const AdjointArgs g,
                                                        const StepArgs a, const PackedRates pr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,13 +117,13 @@ __global__ void __launch_bounds__(128, 3) adjoint2_kernel(const StepIO<T> io, co
     const int xm = (x0 == 0) ? a.g.nx - 1 : x0 - 1;
     const int xp = (x0 + 2 == a.g.nx) ? 0 : x0 + 2;
     const int own = R.own + x0;
-    f2 f[27], mu[27];
-    static_for<27>([&](auto iq) {
+    f2 f[Q], mu[Q];
+    static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
-        constexpr int i = ex<27>(q), j = ey<27>(q) + 1, k = ez<27>(q) + 1;
-        constexpr int o = opposite<27>(q);
-        const f2 v = pull_pair<27, T, kWalls>(io, R, q, x0, xm, xp);
-        f[q] = Storage<T>::kScaled ? v * f2(float(weight<27>(q))) : v;
+        constexpr int i = ex<Q>(q), j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
+        constexpr int o = opposite<Q>(q);
+        const f2 v = pull_pair<Q, T, kWalls>(io, R, q, x0, xm, xp);
+        f[q] = Storage<T>::kScaled ? v * f2(float(weight<Q>(q))) : v;
         if (kWalls && R.wall[2 - j][2 - k]) {
             mu[q] = Pair<float>::ld2(g.lam_next[o] + own);
         } else {
@@ -117,10 +156,10 @@ __global__ void __launch_bounds__(128, 3) adjoint2_kernel(const StepIO<T> io, co
         a1 = f2(g.gF[N + c], g.gF[N + c + 1]);
         a2 = f2(g.gF[2 * N + c], g.gF[2 * N + c + 1]);
     }
-    const Rates27<f2> r = load_rates_packed(pr);
-    f2 lam[27], gx, gy, gz;
-    adjoint27<f2>(f, Fx, Fy, Fz, r, mu, lam, gx, gy, gz);
-    static_for<27>([&](auto iq) {
+    const typename PairRates<Q>::type r = PairRates<Q>::load(pr);
+    f2 lam[Q], gx, gy, gz;
+    adjoint_collide<f2>(f, Fx, Fy, Fz, r, mu, lam, gx, gy, gz);
+    static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
         Pair<float>::st2(g.lam_out[q] + own, lam[q]);
     });
@@ -140,15 +179,15 @@ __global__ void __launch_bounds__(128, 3) adjoint2_kernel(const StepIO<T> io, co
 // Seed of the adjoint for J = sum_x rho |u|^2 / 2 at the final state:
 // lam_a = u.e_a - |u|^2 / 2, and the direct term dJ/dF += u / 2
 // (u = (j + F/2) / rho).
-template <typename T>
+template <int Q, typename T>
 __global__ void __launch_bounds__(128) energy_seed_kernel(const T *__restrict__ buf,
                                                           const StepArgs a, AdjointArgs g) {
     int x, y, z;
     if (!cell_coords(a.g, x, y, z)) return;
-    float f[27];
-    gather<27, T>(buf, a.g, pull_sources(a.g, x, y, z), f);
+    float f[Q];
+    gather<Q, T>(buf, a.g, pull_sources(a.g, x, y, z), f);
     float drho, jx, jy, jz, Fx, Fy, Fz;
-    moments<27>(f, drho, jx, jy, jz);
+    moments<Q>(f, drho, jx, jy, jz);
     const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
     const long long c = dense_index(a.g, x, y, z);
     cell_force(a, c, N, Fx, Fy, Fz);
@@ -157,8 +196,8 @@ __global__ void __launch_bounds__(128) energy_seed_kernel(const T *__restrict__ 
     const float h = 0.5f * (ux * ux + uy * uy + uz * uz);
     const long long own = ((long long)z * a.g.ny + y) * a.g.px + x;
 #pragma unroll
-    for (int q = 0; q < 27; ++q)
-        g.lam_out[q][own] = ex<27>(q) * ux + ey<27>(q) * uy + ez<27>(q) * uz - h;
+    for (int q = 0; q < Q; ++q)
+        g.lam_out[q][own] = ex<Q>(q) * ux + ey<Q>(q) * uy + ez<Q>(q) * uz - h;
     if (g.gF) {
         g.gF[c] += 0.5f * ux;
         g.gF[N + c] += 0.5f * uy;
@@ -172,17 +211,17 @@ __global__ void __launch_bounds__(128) energy_seed_kernel(const T *__restrict__ 
 // d u_i / d f_a = (e_ai - u_i) / rho,
 //     lam_a = g_rho + sum_i (e_ai - u_i) g_u_i / rho,
 // and the direct term dJ/dF_i += g_u_i / (2 rho) (u carries F/2).
-template <typename T>
+template <int Q, typename T>
 __global__ void __launch_bounds__(128) macro_seed_kernel(const T *__restrict__ buf,
                                                          const StepArgs a, AdjointArgs g,
                                                          const float *__restrict__ g_rho,
                                                          const float *__restrict__ g_u) {
     int x, y, z;
     if (!cell_coords(a.g, x, y, z)) return;
-    float f[27];
-    gather<27, T>(buf, a.g, pull_sources(a.g, x, y, z), f);
+    float f[Q];
+    gather<Q, T>(buf, a.g, pull_sources(a.g, x, y, z), f);
     float drho, jx, jy, jz, Fx, Fy, Fz;
-    moments<27>(f, drho, jx, jy, jz);
+    moments<Q>(f, drho, jx, jy, jz);
     const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
     const long long c = dense_index(a.g, x, y, z);
     cell_force(a, c, N, Fx, Fy, Fz);
@@ -195,8 +234,8 @@ __global__ void __launch_bounds__(128) macro_seed_kernel(const T *__restrict__ b
     const float base = gr - (ux * gx + uy * gy + uz * gz);
     const long long own = ((long long)z * a.g.ny + y) * a.g.px + x;
 #pragma unroll
-    for (int q = 0; q < 27; ++q)
-        g.lam_out[q][own] = base + ex<27>(q) * gx + ey<27>(q) * gy + ez<27>(q) * gz;
+    for (int q = 0; q < Q; ++q)
+        g.lam_out[q][own] = base + ex<Q>(q) * gx + ey<Q>(q) * gy + ez<Q>(q) * gz;
     if (g.gF) {
         g.gF[c] += 0.5f * gx;
         g.gF[N + c] += 0.5f * gy;
@@ -240,12 +279,12 @@ __global__ void __launch_bounds__(kRedThreads) energy_kernel(const T *__restrict
     }
 }
 
-template <typename T>
+template <int Q, typename T>
 cudaError_t launch_adjoint(const void *f_t, const float *lam_next, float *lam_out, float *gF,
                            const StepArgs &a, cudaStream_t st) {
     StepIO<T> io;
     AdjointArgs g;
-    for (int q = 0; q < 27; ++q) {
+    for (int q = 0; q < Q; ++q) {
         io.in[q] = static_cast<const T *>(f_t) + q * a.g.pop;
         io.out[q] = nullptr;
         g.lam_next[q] = lam_next + q * a.g.pop;
@@ -258,44 +297,44 @@ cudaError_t launch_adjoint(const void *f_t, const float *lam_next, float *lam_ou
         const CellLaunch L = cell_launch(half);
         const PackedRates pr = packed_rates(a);
         if (a.g.bc)
-            adjoint2_kernel<T, true><<<L.grid, L.block, 0, st>>>(io, g, a, pr);
+            adjoint2_kernel<Q, T, true><<<L.grid, L.block, 0, st>>>(io, g, a, pr);
         else
-            adjoint2_kernel<T, false><<<L.grid, L.block, 0, st>>>(io, g, a, pr);
+            adjoint2_kernel<Q, T, false><<<L.grid, L.block, 0, st>>>(io, g, a, pr);
         return cudaGetLastError();
     }
     const CellLaunch L = cell_launch(a.g);
     if (a.g.bc)
-        adjoint_kernel<T, true><<<L.grid, L.block, 0, st>>>(io, g, a);
+        adjoint_kernel<Q, T, true><<<L.grid, L.block, 0, st>>>(io, g, a);
     else
-        adjoint_kernel<T, false><<<L.grid, L.block, 0, st>>>(io, g, a);
+        adjoint_kernel<Q, T, false><<<L.grid, L.block, 0, st>>>(io, g, a);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <int Q, typename T>
 cudaError_t launch_energy_seed(const void *f, float *lam_out, float *gF, const StepArgs &a,
                                cudaStream_t st) {
     AdjointArgs g;
-    for (int q = 0; q < 27; ++q) {
+    for (int q = 0; q < Q; ++q) {
         g.lam_next[q] = nullptr;
         g.lam_out[q] = lam_out + q * a.g.pop;
     }
     g.gF = gF;
     const CellLaunch L = cell_launch(a.g);
-    energy_seed_kernel<T><<<L.grid, L.block, 0, st>>>(static_cast<const T *>(f), a, g);
+    energy_seed_kernel<Q, T><<<L.grid, L.block, 0, st>>>(static_cast<const T *>(f), a, g);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <int Q, typename T>
 cudaError_t launch_macro_seed(const void *f, const float *g_rho, const float *g_u,
                               float *lam_out, float *gF, const StepArgs &a, cudaStream_t st) {
     AdjointArgs g;
-    for (int q = 0; q < 27; ++q) {
+    for (int q = 0; q < Q; ++q) {
         g.lam_next[q] = nullptr;
         g.lam_out[q] = lam_out + q * a.g.pop;
     }
     g.gF = gF;
     const CellLaunch L = cell_launch(a.g);
-    macro_seed_kernel<T><<<L.grid, L.block, 0, st>>>(static_cast<const T *>(f), a, g, g_rho, g_u);
+    macro_seed_kernel<Q, T><<<L.grid, L.block, 0, st>>>(static_cast<const T *>(f), a, g, g_rho, g_u);
     return cudaGetLastError();
 }
 
@@ -306,17 +345,15 @@ cudaError_t launch_energy(const void *f, const StepArgs &a, double *part, int bl
     return cudaGetLastError();
 }
 
-#define LBM_INSTANTIATE_ADJOINT(EXT, T)                                                          \
-    EXT template cudaError_t launch_adjoint<T>(const void *, const float *, float *, float *,   \
-                                               const StepArgs &, cudaStream_t);                 \
-    EXT template cudaError_t launch_energy_seed<T>(const void *, float *, float *,               \
-                                                   const StepArgs &, cudaStream_t);             \
-    EXT template cudaError_t launch_macro_seed<T>(const void *, const float *, const float *,    \
-                                                  float *, float *, const StepArgs &,           \
-                                                  cudaStream_t);                                \
-    EXT template cudaError_t launch_energy<27, T>(const void *, const StepArgs &, double *, int, \
-                                                  cudaStream_t);                                \
-    EXT template cudaError_t launch_energy<15, T>(const void *, const StepArgs &, double *, int, \
-                                                  cudaStream_t);
+#define LBM_INSTANTIATE_ADJOINT(EXT, Q, T)                                                        \
+    EXT template cudaError_t launch_adjoint<Q, T>(const void *, const float *, float *, float *, \
+                                                  const StepArgs &, cudaStream_t);              \
+    EXT template cudaError_t launch_energy_seed<Q, T>(const void *, float *, float *,            \
+                                                      const StepArgs &, cudaStream_t);          \
+    EXT template cudaError_t launch_macro_seed<Q, T>(const void *, const float *, const float *, \
+                                                     float *, float *, const StepArgs &,        \
+                                                     cudaStream_t);                             \
+    EXT template cudaError_t launch_energy<Q, T>(const void *, const StepArgs &, double *, int,  \
+                                                 cudaStream_t);
 
 }  // namespace lbm

@@ -11,9 +11,12 @@
 namespace lbm {
 LBM_INSTANTIATE(extern, 27)
 LBM_INSTANTIATE(extern, 15)
-LBM_INSTANTIATE_ADJOINT(extern, float)
-LBM_INSTANTIATE_ADJOINT(extern, __half)
-LBM_INSTANTIATE_ADJOINT(extern, __nv_bfloat16)
+LBM_INSTANTIATE_ADJOINT(extern, 27, float)
+LBM_INSTANTIATE_ADJOINT(extern, 15, float)
+LBM_INSTANTIATE_ADJOINT(extern, 27, __half)
+LBM_INSTANTIATE_ADJOINT(extern, 15, __half)
+LBM_INSTANTIATE_ADJOINT(extern, 27, __nv_bfloat16)
+LBM_INSTANTIATE_ADJOINT(extern, 15, __nv_bfloat16)
 }  // namespace lbm
 
 // A captured run of steps (a CUDA graph), valid for the launch arguments,
@@ -126,36 +129,25 @@ cudaError_t dispatch(const lbm_ctx *c, Args &&...args) {
     }
 }
 
-// Dispatch on the storage type only (D3Q27 adjoint kernels).
-template <template <typename> class Fn, typename... Args>
-cudaError_t dispatch_storage(const lbm_ctx *c, Args &&...args) {
-    switch (int(c->storage)) {
-        case LBM_STORE_F32: return Fn<float>::run(args...);
-        case LBM_STORE_F16: return Fn<__half>::run(args...);
-        case LBM_STORE_BF16: return Fn<__nv_bfloat16>::run(args...);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename T>
+template <int Q, typename T>
 struct AdjointFn {
     static cudaError_t run(const void *f, const float *ln, float *lo, float *gF,
                            const lbm::StepArgs &a, cudaStream_t s) {
-        return lbm::launch_adjoint<T>(f, ln, lo, gF, a, s);
+        return lbm::launch_adjoint<Q, T>(f, ln, lo, gF, a, s);
     }
 };
-template <typename T>
+template <int Q, typename T>
 struct SeedFn {
     static cudaError_t run(const void *f, float *lo, float *gF, const lbm::StepArgs &a,
                            cudaStream_t s) {
-        return lbm::launch_energy_seed<T>(f, lo, gF, a, s);
+        return lbm::launch_energy_seed<Q, T>(f, lo, gF, a, s);
     }
 };
-template <typename T>
+template <int Q, typename T>
 struct MacroSeedFn {
     static cudaError_t run(const void *f, const float *g_rho, const float *g_u, float *lo,
                            float *gF, const lbm::StepArgs &a, cudaStream_t s) {
-        return lbm::launch_macro_seed<T>(f, g_rho, g_u, lo, gF, a, s);
+        return lbm::launch_macro_seed<Q, T>(f, g_rho, g_u, lo, gF, a, s);
     }
 };
 template <int Q, typename T>
@@ -542,10 +534,9 @@ lbm_status lbm_adjoint_step(lbm_ctx *c, const void *f_t, const float *lam_next, 
     if ((reinterpret_cast<uintptr_t>(lam_next) | reinterpret_cast<uintptr_t>(lam_out)) & 15u)
         return LBM_EINVAL;
     if (dJdF && (reinterpret_cast<uintptr_t>(dJdF) & 3u)) return LBM_EINVAL;
-    if (c->Q != 27 || c->inplace) return LBM_EUNSUPPORTED;
+    if (c->inplace) return LBM_EUNSUPPORTED;
     const lbm::StepArgs a = step_args(c);
-    cudaError_t e = dispatch_storage<AdjointFn>(c, f_t, lam_next, lam_out, dJdF, a,
-                                                (cudaStream_t)stream);
+    cudaError_t e = dispatch<AdjointFn>(c, f_t, lam_next, lam_out, dJdF, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     return LBM_OK;
 }
@@ -561,8 +552,7 @@ lbm_status lbm_kinetic_energy_seed(lbm_ctx *c, const void *f, float *lam_out, fl
         a.g.layout = lbm::kPull;  // a caller's buffer holds a two-buffer state
     }
     if (!state_buffer_ok(f) || (reinterpret_cast<uintptr_t>(lam_out) & 15u)) return LBM_EINVAL;
-    if (c->Q != 27) return LBM_EUNSUPPORTED;
-    cudaError_t e = dispatch_storage<SeedFn>(c, f, lam_out, dJdF, a, (cudaStream_t)stream);
+    cudaError_t e = dispatch<SeedFn>(c, f, lam_out, dJdF, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     return LBM_OK;
 }
@@ -581,9 +571,8 @@ lbm_status lbm_macroscopic_seed(lbm_ctx *c, const void *f, const float *g_rho, c
     if ((reinterpret_cast<uintptr_t>(g_rho) | reinterpret_cast<uintptr_t>(g_u) |
          reinterpret_cast<uintptr_t>(dJdF)) & 3u)
         return LBM_EINVAL;
-    if (c->Q != 27) return LBM_EUNSUPPORTED;
-    cudaError_t e = dispatch_storage<MacroSeedFn>(c, f, g_rho, g_u, lam_out, dJdF, a,
-                                                  (cudaStream_t)stream);
+    cudaError_t e = dispatch<MacroSeedFn>(c, f, g_rho, g_u, lam_out, dJdF, a,
+                                        (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     return LBM_OK;
 }

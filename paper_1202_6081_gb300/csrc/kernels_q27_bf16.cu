@@ -4,5 +4,5 @@
 
 namespace lbm {
 LBM_INSTANTIATE_1(, 27, __nv_bfloat16)
-LBM_INSTANTIATE_ADJOINT(, __nv_bfloat16)
+LBM_INSTANTIATE_ADJOINT(, 27, __nv_bfloat16)
 }  // namespace lbm

@@ -4,5 +4,5 @@
 
 namespace lbm {
 LBM_INSTANTIATE_1(, 27, __half)
-LBM_INSTANTIATE_ADJOINT(, __half)
+LBM_INSTANTIATE_ADJOINT(, 27, __half)
 }  // namespace lbm

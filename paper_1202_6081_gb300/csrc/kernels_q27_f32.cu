@@ -4,5 +4,5 @@
 
 namespace lbm {
 LBM_INSTANTIATE_1(, 27, float)
-LBM_INSTANTIATE_ADJOINT(, float)
+LBM_INSTANTIATE_ADJOINT(, 27, float)
 }  // namespace lbm

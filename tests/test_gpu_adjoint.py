@@ -1,5 +1,5 @@
-"""The discrete adjoint on the GPU (through the C ABI) against the FP64
-oracle's adjoint (complex-step Jacobians), against FP64 central finite
+"""The discrete adjoint on the GPU (through the C ABI), D3Q27 and D3Q15,
+against the FP64 oracle's adjoint (complex-step Jacobians), against FP64 central finite
 differences of the oracle, and, at the 128^3 workload, against central
 finite differences of the GPU forward.
 
@@ -43,11 +43,11 @@ def to_pitched(S, dense):
     return lam
 
 
+@pytest.mark.parametrize("Q", [27, 15])
 @pytest.mark.parametrize("bc", [0, 3])
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 @pytest.mark.parametrize("shape", [(6, 7, 10), (6, 7, 9)])  # two-cell and one-cell kernels
-def test_adjoint_step_matches_oracle(lbm, orc, bc, storage, shape):
-    Q = 27
+def test_adjoint_step_matches_oracle(lbm, orc, Q, bc, storage, shape):
     rho, u = W.taylor_green(shape, u0=0.05, noise=1e-2, seed=31)
     om = W.random_omegas(Q, seed=32)
     F = f32(W.rng(33).uniform(-1e-3, 1e-3, (3,) + shape))
@@ -68,8 +68,8 @@ def test_adjoint_step_matches_oracle(lbm, orc, bc, storage, shape):
     assert np.abs(gF.cpu().numpy() - gF_want).max() <= 1e-5 * np.abs(gF_want).max()
 
 
-def test_kinetic_energy_and_seed_match_oracle(lbm, orc):
-    Q = 27
+@pytest.mark.parametrize("Q", [27, 15])
+def test_kinetic_energy_and_seed_match_oracle(lbm, orc, Q):
     shape = (5, 8, 12)
     rho, u = W.taylor_green(shape, u0=0.05, noise=1e-2, seed=35)
     F = f32(W.rng(36).uniform(-1e-3, 1e-3, (3,) + shape))
@@ -174,11 +174,11 @@ def test_gradient_128cubed_matches_gpu_finite_differences(lbm):
     assert np.abs(got - fd).max() <= 1e-3 * np.abs(fd).max()
 
 
+@pytest.mark.parametrize("Q", [27, 15])
 @pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_macroscopic_seed_matches_oracle(lbm, orc, storage):
+def test_macroscopic_seed_matches_oracle(lbm, orc, Q, storage):
     """Seed of the adjoint for an objective J(rho, u): lam = dJ/df and the
     direct dJ/dF against the oracle's chain rule, walled grid, force field."""
-    Q = 27
     shape = (5, 7, 10)
     rho, u = W.taylor_green(shape, u0=0.05, noise=1e-2, seed=51)
     F = f32(W.rng(52).uniform(-1e-3, 1e-3, (3,) + shape))
@@ -203,13 +203,13 @@ def test_macroscopic_seed_matches_oracle(lbm, orc, storage):
     assert np.abs(S.adjoint_view(lam).cpu().numpy() - want0).max() <= 1e-5 * np.abs(want0).max()
 
 
-def test_macroscopic_after_gradients_match_fp64_differences(lbm, orc):
+@pytest.mark.parametrize("Q", [27, 15])
+def test_macroscopic_after_gradients_match_fp64_differences(lbm, orc, Q):
     """A torch objective of the final (rho, u), J = <c, u> + <d, rho^2>, back-
     propagated through 30 steps (checkpoints every 7, so the last segment is
     short) on a walled 6 x 8 x 10 grid: dJ/dF and dJ/df0 match FP64 central
     differences of the oracle on 12 sampled entries each."""
     from paper_1202_6081_gb300.autograd import macroscopic_after
-    Q = 27
     shape = (6, 8, 10)
     om = W.omegas(Q, 1 / 0.7)
     rho0, u0 = W.taylor_green(shape, u0=0.03, noise=2e-3, seed=55)
