@@ -243,7 +243,9 @@ lbm_status lbm_kinetic_energy(lbm_ctx *ctx, const void *f, double *out, void *st
 
 /* Seed of the adjoint of J: lam_out = dJ/df of the state in f (NULL =
  * current), lam_a = u.e_a - |u|^2/2, and, when dJdF is not NULL, the direct
- * term dJdF += u/2.  Errors: LBM_EINVAL, LBM_ESTATE, LBM_ECUDA. */
+ * term dJdF += u/2.  lam_out: an adjoint field (lbm_adjoint_bytes, 16-byte
+ * aligned); dJdF: device FP32 [3][nz][ny][nx], 4-byte aligned, accumulated.
+ * Errors: LBM_EINVAL, LBM_ESTATE, LBM_ECUDA. */
 lbm_status lbm_kinetic_energy_seed(lbm_ctx *ctx, const void *f, float *lam_out, float *dJdF,
                                    void *stream);
 

@@ -282,8 +282,8 @@ __global__ void __launch_bounds__(kRedThreads) energy_kernel(const T *__restrict
 template <int Q, typename T>
 cudaError_t launch_adjoint(const void *f_t, const float *lam_next, float *lam_out, float *gF,
                            const StepArgs &a, cudaStream_t st) {
-    StepIO<T> io;
-    AdjointArgs g;
+    StepIO<T> io{};  // slots q >= Q stay null
+    AdjointArgs g{};
     for (int q = 0; q < Q; ++q) {
         io.in[q] = static_cast<const T *>(f_t) + q * a.g.pop;
         io.out[q] = nullptr;
@@ -313,7 +313,7 @@ cudaError_t launch_adjoint(const void *f_t, const float *lam_next, float *lam_ou
 template <int Q, typename T>
 cudaError_t launch_energy_seed(const void *f, float *lam_out, float *gF, const StepArgs &a,
                                cudaStream_t st) {
-    AdjointArgs g;
+    AdjointArgs g{};
     for (int q = 0; q < Q; ++q) {
         g.lam_next[q] = nullptr;
         g.lam_out[q] = lam_out + q * a.g.pop;
@@ -327,7 +327,7 @@ cudaError_t launch_energy_seed(const void *f, float *lam_out, float *gF, const S
 template <int Q, typename T>
 cudaError_t launch_macro_seed(const void *f, const float *g_rho, const float *g_u,
                               float *lam_out, float *gF, const StepArgs &a, cudaStream_t st) {
-    AdjointArgs g;
+    AdjointArgs g{};
     for (int q = 0; q < Q; ++q) {
         g.lam_next[q] = nullptr;
         g.lam_out[q] = lam_out + q * a.g.pop;

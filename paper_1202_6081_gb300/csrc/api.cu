@@ -552,6 +552,7 @@ lbm_status lbm_kinetic_energy_seed(lbm_ctx *c, const void *f, float *lam_out, fl
         a.g.layout = lbm::kPull;  // a caller's buffer holds a two-buffer state
     }
     if (!state_buffer_ok(f) || (reinterpret_cast<uintptr_t>(lam_out) & 15u)) return LBM_EINVAL;
+    if (reinterpret_cast<uintptr_t>(dJdF) & 3u) return LBM_EINVAL;
     cudaError_t e = dispatch<SeedFn>(c, f, lam_out, dJdF, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     return LBM_OK;

@@ -251,3 +251,50 @@ def test_macroscopic_after_gradients_match_fp64_differences(lbm, orc, Q):
     print("dJ/dF fd", fdF[:3], "adjoint", gotF[:3], "; dJ/df0 fd", fdf[:3], "adjoint", gotf[:3])
     assert np.abs(gotF - fdF).max() <= 1e-3 * np.abs(fdF).max()
     assert np.abs(gotf - fdf).max() <= 1e-3 * np.abs(fdf).max()
+
+
+@pytest.mark.parametrize("Q", [27, 15])
+def test_adjoint_entry_points_reject_bad_arguments(lbm, Q):
+    """The adjoint calls check their pointers before launching anything:
+    misaligned or aliased adjoint fields, a misaligned dJ/dF, a state buffer
+    off its 256-byte alignment and a seed before any state are LBM_EINVAL /
+    LBM_ESTATE; the same call with good arguments succeeds."""
+    import ctypes
+    lib = lbm.load()
+    shape = (4, 5, 6)
+    ctx = lbm.lbm_create(Q, shape[2], shape[1], shape[0], W.omegas(Q, 1.2))
+    try:
+        nb = lbm.lbm_state_bytes(ctx)
+        a = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        b = torch.empty_like(a)
+        p = lambda t, off=0: ctypes.c_void_p(t.data_ptr() + off)
+        lam = torch.zeros(lbm.lbm_adjoint_bytes(ctx) // 4 + 4, dtype=torch.float32, device="cuda")
+        lam2 = torch.zeros_like(lam)
+        gF = torch.zeros(3 * 120 + 1, dtype=torch.float32, device="cuda")
+        seed = lib.lbm_kinetic_energy_seed
+        msd = lib.lbm_macroscopic_seed
+        assert seed(ctx, None, p(lam), None, None) == 3             # no state bound yet
+        assert msd(ctx, None, None, None, p(lam), None, None) == 3
+        assert lib.lbm_bind(ctx, p(a), p(b), None) == 0
+        lbm.lbm_init_equilibrium(ctx, torch.ones(shape, dtype=torch.float64, device="cuda"),
+                                 torch.zeros((3,) + shape, dtype=torch.float64, device="cuda"))
+        step = lib.lbm_adjoint_step
+        assert step(ctx, p(a), p(lam), p(lam), None, None) == 1       # aliased fields
+        assert step(ctx, p(a), p(lam, 4), p(lam2), None, None) == 1   # lam_next misaligned
+        assert step(ctx, p(a), p(lam), p(lam2, 8), None, None) == 1   # lam_out misaligned
+        assert step(ctx, p(a), p(lam), p(lam2), p(gF, 2), None) == 1  # dJ/dF misaligned
+        assert step(ctx, p(a, 16), p(lam), p(lam2), None, None) == 1  # state off 256 B
+        assert step(ctx, None, p(lam), p(lam2), None, None) == 1
+        assert seed(ctx, None, p(lam, 4), None, None) == 1
+        assert seed(ctx, None, p(lam), p(gF, 2), None) == 1
+        assert msd(ctx, None, None, None, p(lam, 8), None, None) == 1
+        assert msd(ctx, None, None, p(gF, 2), p(lam), None, None) == 1
+        # good arguments (dJ/dF at a 4-byte offset is allowed)
+        assert step(ctx, p(a), p(lam), p(lam2), p(gF, 4), None) == 0
+        assert seed(ctx, None, p(lam), p(gF, 4), None) == 0
+        assert msd(ctx, None, None, None, p(lam), p(gF, 4), None) == 0
+        torch.cuda.synchronize()
+        assert not lib.lbm_last_cuda_error(ctx)
+    finally:
+        torch.cuda.synchronize()
+        lbm.lbm_destroy(ctx)
