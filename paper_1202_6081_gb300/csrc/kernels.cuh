@@ -305,12 +305,17 @@ __global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const Ste
 // the collision in packed f32x2 arithmetic.  nx must be even.  Loads of
 // populations with e_x = 0 and all stores are aligned 2-element accesses;
 // e_x = +-1 sources are two single loads (x0 - 1, x0) or (x0 + 1, x0 + 2).
-// 5 blocks of 128 per SM: FP32 storage fits in 96 registers; 16-bit storage
-// spills 72 bytes there but runs faster than at 4 blocks (40.2k vs 38.0k
-// MLUPS FP16 at 512^3).
+// Blocks of 128 per SM: FP32 storage 5 (96 registers, no spills); 16-bit
+// storage 6 (80 registers, ~260 bytes of spills), measured at 512^3: FP16
+// 38.0k / 40.1k / 42.3k / 38.5k / 25.1k MLUPS at 4 / 5 / 6 / 7 / 8 blocks,
+// BF16 39.2k at 5 and 42.2k at 6.
+template <typename T>
+constexpr int kStep2Blocks = Storage<T>::kScaled ? 6 : 5;
+
 template <typename T, bool kWalls>
-__global__ void __launch_bounds__(128, 5) step2_kernel(const StepIO<T> io, const StepArgs a,
-                                                    const PackedRates pr) {
+__global__ void __launch_bounds__(128, kStep2Blocks<T>) step2_kernel(const StepIO<T> io,
+                                                                  const StepArgs a,
+                                                                  const PackedRates pr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
     const int x0 = 2 * t;
