@@ -305,10 +305,11 @@ __global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const Ste
 // the collision in packed f32x2 arithmetic.  nx must be even.  Loads of
 // populations with e_x = 0 and all stores are aligned 2-element accesses;
 // e_x = +-1 sources are two single loads (x0 - 1, x0) or (x0 + 1, x0 + 2).
-// Blocks of 128 per SM: FP32 storage 5 (96 registers, no spills); 16-bit
-// storage 6 (80 registers, ~260 bytes of spills), measured at 512^3: FP16
-// 38.0k / 40.1k / 42.3k / 38.5k / 25.1k MLUPS at 4 / 5 / 6 / 7 / 8 blocks,
-// BF16 39.2k at 5 and 42.2k at 6.
+// Blocks of 128 per SM, by measurement: FP32 storage 5 (96 registers, no
+// spills; 6 blocks ran the same, 32.20k vs 32.23k MLUPS at 256^3, and 7
+// slower); 16-bit storage 6 (80 registers, ~260 bytes of spills): FP16
+// 38.0k / 40.1k / 42.3k / 38.5k / 25.1k MLUPS at 4 / 5 / 6 / 7 / 8 blocks at
+// 512^3, BF16 39.2k at 5 and 42.2k at 6.
 template <typename T>
 constexpr int kStep2Blocks = Storage<T>::kScaled ? 6 : 5;
 
