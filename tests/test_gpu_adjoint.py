@@ -257,8 +257,9 @@ def test_macroscopic_after_gradients_match_fp64_differences(lbm, orc, Q):
 def test_adjoint_entry_points_reject_bad_arguments(lbm, Q):
     """The adjoint calls check their pointers before launching anything:
     misaligned or aliased adjoint fields, a misaligned dJ/dF, a state buffer
-    off its 256-byte alignment and a seed before any state are LBM_EINVAL /
-    LBM_ESTATE; the same call with good arguments succeeds."""
+    off its 256-byte alignment, overlapping state buffers for lbm_step_into
+    and a seed before any state are LBM_EINVAL / LBM_ESTATE; the same call
+    with good arguments succeeds."""
     import ctypes
     lib = lbm.load()
     shape = (4, 5, 6)
@@ -289,6 +290,10 @@ def test_adjoint_entry_points_reject_bad_arguments(lbm, Q):
         assert seed(ctx, None, p(lam), p(gF, 2), None) == 1
         assert msd(ctx, None, None, None, p(lam, 8), None, None) == 1
         assert msd(ctx, None, None, p(gF, 2), p(lam), None, None) == 1
+        # lbm_step_into: same or overlapping state buffers, or one off 256 B
+        assert lib.lbm_step_into(ctx, p(a), p(a), None) == 1
+        assert lib.lbm_step_into(ctx, p(a), p(a, 256), None) == 1
+        assert lib.lbm_step_into(ctx, p(a), p(b, 128), None) == 1
         # good arguments (dJ/dF at a 4-byte offset is allowed)
         assert step(ctx, p(a), p(lam), p(lam2), p(gF, 4), None) == 0
         assert seed(ctx, None, p(lam), p(gF, 4), None) == 0
