@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "D3Q27 fused step MLUPS and % of HBM roofline; adjoint/forward step-time ratio"
 UNIT = "MLUPS"
 BYTES_PER_CELL = {("q27", "f32"): 216, ("q27", "f16"): 108, ("q27", "bf16"): 108,
-                  ("q15", "f32"): 120}
+                  ("q15", "f32"): 120, ("q15", "f16"): 60, ("q15", "bf16"): 60}
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ["lattice.cuh", "vec2.cuh", "collide_q27.cuh", "kernels.cuh"]
 
@@ -505,6 +505,16 @@ def run_ours(args):
             del S
             torch.cuda.empty_cache()
         result["storage_512"] = s16
+        q15 = {}
+        for st in ("f32", "f16", "bf16"):
+            S, _, _ = make_solver(lbm, 15, size, st, 0.6)
+            t = time_steps(torch, S, 200, 5)
+            bpc = (4 if st == "f32" else 2) * 2 * 15
+            q15[st] = {"mlups": cells * 200 / t / 1e6, "GB/s": bpc * cells * 200 / t / 1e9,
+                       "frac": bpc * cells * 200 / t / 1e9 / peak}
+            del S
+            torch.cuda.empty_cache()
+        result["d3q15_%d" % size] = q15
         aa = {}
         for n, st in ((size, "f32"), (512, "f32"), (512, "f16")):
             S, _, _ = make_solver(lbm, 27, n, st, 0.6, inplace=True)
