@@ -104,8 +104,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const StepIO<T> io, const 
 // aligned pair, for e_x = +1 the cells (x0 + 1, x0 + 2), for e_x = -1
 // (x0 - 1, x0).
 // 3 blocks of 128 threads per SM: 168 registers.  D3Q27 spills a few of its
-// 242 there but beats 2 blocks; D3Q15 fits without spills and beats 4
-// blocks (276 B of spills; 0.098 vs 0.090 ms at 128^3).
+// 242 there but beats 2 blocks and 4 (128 registers, ~700 B of spills:
+// 0.206 vs 0.135 ms at 128^3); D3Q15 fits without spills and beats 4 blocks
+// (276 B of spills; 0.098 vs 0.090 ms).
 template <int Q, typename T, bool kWalls>
 __global__ void __launch_bounds__(128, 3) adjoint2_kernel(const StepIO<T> io, const AdjointArgs g,
                                                        const StepArgs a, const PackedRates pr) {
