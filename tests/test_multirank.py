@@ -1,6 +1,7 @@
-"""The bench's multi-rank path on CPU (gloo, world size 2): every rank times
-its own replica, the job reports the slowest rank's time, and the reference
-arm runs on rank 0 only."""
+"""The bench's host logic on CPU: the multi-rank path (gloo, world size 2)
+where every rank times its own replica, the job reports the slowest rank's
+time and the reference arm runs on rank 0 only; and the clock record that
+flags throttling."""
 import os
 import socket
 import sys
@@ -77,3 +78,19 @@ def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_clock_summary_flags_throttling():
+    """The clock record beside every bench line: median SM clock, maximum,
+    and each throttle reason seen active in any sample (nvidia-smi CSV in
+    the sampler's field order); unparsable lines are skipped."""
+    import bench
+    ok = ["2070, 2070, 900.1, Not Active, Not Active, Not Active, Not Active"] * 4
+    s = bench.ClockSampler.summarize(ok + ["[N/A], 2070, 0, x, x, x, x", "garbage"])
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 4}
+    hot = ok + ["1800, 2070, 1400.0, Not Active, Active, Not Active, Active",
+                "1700, 2070, 1400.0, Active, Not Active, Not Active, Not Active"]
+    s = bench.ClockSampler.summarize(hot)
+    assert s["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_power_cap"]
+    assert s["sm_mhz"] == 2070.0 and s["samples"] == 6
+    assert bench.ClockSampler.summarize([]) is None
