@@ -34,6 +34,7 @@ UNIT = "MLUPS"
 BYTES_PER_CELL = {("q27", "f32"): 216, ("q27", "f16"): 108, ("q27", "bf16"): 108,
                   ("q15", "f32"): 120, ("q15", "f16"): 60, ("q15", "bf16"): 60}
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth (a copy reaches ~86 % of it)
 KERNEL_SOURCES = ["lattice.cuh", "vec2.cuh", "collide_q27.cuh", "kernels.cuh"]
 
 
@@ -481,8 +482,11 @@ def run_ours(args):
                      "frac": achieved / peak,
                      "traffic": ncu_traffic(size) if (lat, st, args.inplace) == (27, "f32", False)
                      else None,
-                     "peak_source": "%s hbm_gbs (copy), %d B/cell algorithmic" % (
-                         peak_kind, bpc)},
+                     "peak_source": "%s hbm_gbs: the bandwidth of a plain device copy "
+                                    "(frac is achieved / measured copy, not of the data sheet), "
+                                    "%d B/cell algorithmic" % (peak_kind, bpc),
+                     "nominal_peak": NOMINAL_HBM_GBS,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "conservation": {"mass": cons[0], "momentum": list(cons[1:])},

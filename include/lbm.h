@@ -229,7 +229,8 @@ lbm_status lbm_step_into(lbm_ctx *ctx, const void *f_in, void *f_out, void *stre
  *     dJdF(y) += (dC/dF(y))^T mu(y)
  * (device FP32 [3][nz][ny][nx], accumulated; the force of step t is the
  * bound force field or the uniform force).  lam_next, lam_out: device FP32
- * adjoint fields (lbm_adjoint_bytes, 16-byte aligned, distinct).
+ * adjoint fields (lbm_adjoint_bytes, 16-byte aligned, not overlapping: the
+ * step reads lam_next at neighbouring cells while it writes lam_out).
  * Errors: LBM_EINVAL, LBM_EUNSUPPORTED (LBM_INPLACE context), LBM_ECUDA. */
 lbm_status lbm_adjoint_step(lbm_ctx *ctx, const void *f_t, const float *lam_next,
                             float *lam_out, float *dJdF, void *stream);
@@ -270,15 +271,20 @@ lbm_status lbm_macroscopic_seed(lbm_ctx *ctx, const void *f, const float *g_rho,
  * no cudaMalloc or cudaFree: the per-row partial sums live in a fixed array
  * inside the library, 2 MiB per GPU, held by every GPU that loads the
  * library until the process exits.
- *   out  device, 4 doubles (8-byte aligned): sum_x (rho - 1), then
- *        sum_x rho u_x, rho u_y, rho u_z.  Note: the first value is the mass
- *        minus the cell count nx*ny*nz (the FP64 sum of the density
- *        deviations, without the large constant).
+ *   out  4 doubles (8-byte aligned) that the context's GPU can write:
+ *        its own device memory, managed memory, or page-locked host memory
+ *        mapped into its address space (anything else, e.g. a plain host
+ *        array, is refused with LBM_EINVAL before any launch):
+ *        sum_x (rho - 1), then sum_x rho u_x, rho u_y, rho u_z.  Note: the
+ *        first value is the mass minus the cell count nx*ny*nz (the FP64
+ *        sum of the density deviations, without the large constant).
  * Limit: ny * nz <= 65536 (one partial record per (y, z) row); larger grids
  * return LBM_EINVAL.  The context's device must be current (LBM_ESTATE
  * otherwise).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * address (cudaGetSymbolAddress) and keeps it for the life of the process;
+ * make that first call before any stream capture, and make no call after a
+ * cudaDeviceReset of that device (the kept address would no longer be
+ * valid).  All calls share the array: calls whose work overlaps on the GPU
  * race.  Errors: LBM_EINVAL, LBM_ESTATE, LBM_ECUDA, LBM_EUNSUPPORTED (device
  * index >= 64). */
 lbm_status lbm_conservation_noalloc(lbm_ctx *ctx, double *out, void *stream);

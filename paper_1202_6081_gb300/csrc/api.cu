@@ -533,6 +533,14 @@ lbm_status lbm_adjoint_step(lbm_ctx *c, const void *f_t, const float *lam_next, 
         return LBM_EINVAL;
     if ((reinterpret_cast<uintptr_t>(lam_next) | reinterpret_cast<uintptr_t>(lam_out)) & 15u)
         return LBM_EINVAL;
+    {
+        // the step pulls lam_next from neighbouring cells while writing
+        // lam_out: the two fields must not share any byte
+        const size_t bytes = lbm_adjoint_bytes(c);
+        const char *a = reinterpret_cast<const char *>(lam_next);
+        const char *b = reinterpret_cast<const char *>(lam_out);
+        if (a < b + bytes && b < a + bytes) return LBM_EINVAL;
+    }
     if (dJdF && (reinterpret_cast<uintptr_t>(dJdF) & 3u)) return LBM_EINVAL;
     if (c->inplace) return LBM_EUNSUPPORTED;
     const lbm::StepArgs a = step_args(c);
@@ -652,6 +660,34 @@ lbm_status noalloc_scratch(int device, double **out) {
 }
 }  // namespace
 
+// Address through which the context's GPU writes the 4 results at `out`:
+// device memory of that GPU, managed memory, or page-locked host memory
+// mapped into the GPU's address space.  Plain (pageable) host memory and
+// another GPU's memory are refused, before anything is launched: a kernel
+// writing there would fault.
+static lbm_status device_result_ptr(const lbm_ctx *c, double *out, double **dev_out) {
+    cudaPointerAttributes at;
+    std::memset(&at, 0, sizeof(at));
+    if (cudaPointerGetAttributes(&at, out) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_EINVAL;
+    }
+    switch (at.type) {
+        case cudaMemoryTypeDevice:
+            if (at.device != c->device) return LBM_EINVAL;
+            *dev_out = static_cast<double *>(at.devicePointer);
+            return *dev_out ? LBM_OK : LBM_EINVAL;
+        case cudaMemoryTypeManaged:
+            *dev_out = out;
+            return LBM_OK;
+        case cudaMemoryTypeHost:
+            *dev_out = static_cast<double *>(at.devicePointer);  // NULL if not mapped
+            return *dev_out ? LBM_OK : LBM_EINVAL;
+        default:
+            return LBM_EINVAL;
+    }
+}
+
 lbm_status lbm_conservation_noalloc(lbm_ctx *c, double *out, void *stream) {
     if (!c || !out || (reinterpret_cast<uintptr_t>(out) & 7u)) return LBM_EINVAL;
     if (!c->bound || !c->state_set) return LBM_ESTATE;
@@ -660,6 +696,9 @@ lbm_status lbm_conservation_noalloc(lbm_ctx *c, double *out, void *stream) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
     if (dev != c->device) return LBM_ESTATE;  // the context's device must be current
+    double *dout = nullptr;
+    const lbm_status ps = device_result_ptr(c, out, &dout);
+    if (ps != LBM_OK) return ps;
     double *part = nullptr;
     const lbm_status st = noalloc_scratch(dev, &part);
     if (st != LBM_OK) return st;
@@ -667,7 +706,7 @@ lbm_status lbm_conservation_noalloc(lbm_ctx *c, double *out, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = dispatch<ConsFn>(c, (const void *)c->buf[c->cur], a, part, int(rows), s);
     if (e != cudaSuccess) return cuda_fail(c, e);
-    e = lbm::launch_reduce_final(part, int(rows), out, s);
+    e = lbm::launch_reduce_final(part, int(rows), dout, s);
     if (e != cudaSuccess) return cuda_fail(c, e);
     return LBM_OK;
 }

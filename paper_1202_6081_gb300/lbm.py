@@ -236,6 +236,10 @@ def lbm_kinetic_energy(ctx, f=None, stream=None):
 def lbm_conservation_noalloc(ctx, out, stream=None):
     """Asynchronous conservation sums into the device tensor `out` (4 FP64:
     sum (rho - 1), sum rho u) without any allocation by the library."""
+    if not (torch.is_tensor(out) and out.is_cuda and out.dtype == torch.float64
+            and out.numel() >= 4 and out.is_contiguous()):
+        raise ValueError("lbm_conservation_noalloc: out must be a contiguous CUDA float64 "
+                         "tensor of at least 4 elements")
     _check(load().lbm_conservation_noalloc(ctx, _ptr(out), _stream(stream)),
            "lbm_conservation_noalloc", ctx)
 

@@ -303,3 +303,23 @@ def test_adjoint_entry_points_reject_bad_arguments(lbm, Q):
     finally:
         torch.cuda.synchronize()
         lbm.lbm_destroy(ctx)
+
+
+def test_adjoint_step_refuses_overlapping_fields(lbm):
+    """The adjoint step reads lam_next at neighbouring cells while it writes
+    lam_out, so two fields that share any byte are refused (LBM_EINVAL)
+    before anything is launched; fields that only touch are accepted."""
+    shape = (4, 6, 8)
+    S = lbm.Solver(27, shape, W.omegas(27, 1.2))
+    S.init_equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    n = lbm.lbm_adjoint_bytes(S.ctx) // 4
+    pool = torch.zeros(2 * n + 64, dtype=torch.float32, device="cuda")
+    for off in (4, n - 4):  # 16-byte aligned partial overlaps, both directions
+        with pytest.raises(lbm.LBMError) as err:
+            S.adjoint_step(S.current_buffer(), pool[:n], pool[off:off + n])
+        assert err.value.status == 1
+        with pytest.raises(lbm.LBMError) as err:
+            S.adjoint_step(S.current_buffer(), pool[off:off + n], pool[:n])
+        assert err.value.status == 1
+    S.adjoint_step(S.current_buffer(), pool[:n], pool[n:2 * n])
+    torch.cuda.synchronize()

@@ -371,14 +371,43 @@ def test_16bit_storage_512cubed_500_steps_vs_fp32(lbm):
     assert errs["bf16"] <= 5e-3
 
 
-def test_full_size_sampled_step_256(lbm, orc):
+@pytest.mark.parametrize("tau", [0.51, 1.0])
+def test_tau_sweep_extremes_64cubed_100_steps(lbm, orc, tau):
+    """The tau sweep's workload (D3Q27 Taylor-Green + noise, periodic, FP32
+    storage, the two-cell kernel the bench times) at the ends of the sweep:
+    tau = 0.51 (omega_nu = 1.961, the strongest over-relaxation, where the
+    factor 1 - omega = -0.96 of every relaxed moment is closest to -1) and
+    tau = 1.0, 64^3 x 100 steps.  Density and velocity within 1e-5 relative
+    L2 of the FP64 oracle, the density fluctuation within 1e-3.  (Rates and
+    viscosity: the relation at the end of Sec. 7.)"""
+    Q = 27
+    shape = (64, 64, 64)
+    om = W.omegas(Q, 1 / tau)
+    rho0, u0 = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    S = lbm.Solver(Q, shape, om)
+    S.init_equilibrium(rho0, u0)
+    S.step(100)
+    f_gpu = gpu_state(S)
+    f_or = orc.run(Q, shape, orc.equilibrium(Q, rho0, u0, np.zeros(3)), np.zeros(3), om, 100)
+    r_g, u_g = orc.macroscopic(Q, f_gpu, np.zeros(3))
+    r_o, u_o = orc.macroscopic(Q, f_or, np.zeros(3))
+    eu, er, er1 = rel_l2(u_g, u_o), rel_l2(r_g, r_o), rel_l2(r_g - 1, r_o - 1)
+    print("tau %.2f: rel L2 u %.2e, rho %.2e, rho - 1 %.2e" % (tau, eu, er, er1))
+    assert eu <= 1e-5
+    assert er <= 1e-5
+    assert er1 <= 1e-3
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.51])
+def test_full_size_sampled_step_256(lbm, orc, tau):
     """The 256^3 Taylor-Green + noise workload in the bench's launch
-    configuration: after 5 GPU steps, one more GPU step is checked on 16
-    sampled cells against the oracle's collision of the 27 upstream cells,
-    and mass and momentum are conserved."""
+    configuration (tau = 0.6, and the sweep's tau = 0.51): after 5 GPU steps,
+    one more GPU step is checked on 16 sampled cells against the oracle's
+    collision of the 27 upstream cells, and mass and momentum are
+    conserved."""
     Q = 27
     shape = (256, 256, 256)
-    om = W.omegas(Q, 1 / 0.6)
+    om = W.omegas(Q, 1 / tau)
     rho0, u0 = W.taylor_green(shape, u0=0.02, noise=1e-3)
     S = lbm.Solver(Q, shape, om)
     S.init_equilibrium(rho0, u0)
