@@ -173,12 +173,12 @@ struct Pair<float> {
 template <typename T>
 struct Pair16 {
     template <int q>
-    __device__ __forceinline__ static void st2s(T *p, f2 v, unsigned salt) {
-        __stcs(reinterpret_cast<unsigned int *>(p), pack_sr<T, q>(v.lo(), v.hi(), salt));
+    __device__ __forceinline__ static void st2s(T *p, f2 v, unsigned seed) {
+        __stcs(reinterpret_cast<unsigned int *>(p), pack_sr<T, q>(v.lo(), v.hi(), seed));
     }
     template <int q>
-    __device__ __forceinline__ static void st1x2s(T *plo, T *phi, f2 v, unsigned salt) {
-        const unsigned d = pack_sr<T, q>(v.lo(), v.hi(), salt);
+    __device__ __forceinline__ static void st1x2s(T *plo, T *phi, f2 v, unsigned seed) {
+        const unsigned d = pack_sr<T, q>(v.lo(), v.hi(), seed);
         __stcs(reinterpret_cast<unsigned short *>(plo), static_cast<unsigned short>(d & 0xffffu));
         __stcs(reinterpret_cast<unsigned short *>(phi), static_cast<unsigned short>(d >> 16));
     }
@@ -203,6 +203,21 @@ struct Pair<__nv_bfloat16> : Pair16<__nv_bfloat16> {
         return __bfloat162float(__ldg(p));
     }
 };
+
+// Seed of a thread's stochastic rounding (sr_seed) from four of its
+// pre-collision values, of different directions, and its position.
+template <int Q>
+constexpr int kSeedPop = Q == 27 ? 11 : 9;
+template <int Q>
+__device__ __forceinline__ unsigned pair_seed(const f2 (&f)[Q], int own) {
+    return sr_seed(f[1].v ^ f[6].v ^ f[kSeedPop<Q>].v ^ f[Q - 1].v, own);
+}
+template <int Q>
+__device__ __forceinline__ unsigned cell_seed(const float (&f)[Q], int own) {
+    const unsigned a = __float_as_uint(f[1]) ^ __float_as_uint(f[6]);
+    const unsigned b = __float_as_uint(f[kSeedPop<Q>]) ^ __float_as_uint(f[Q - 1]);
+    return sr_seed(static_cast<unsigned long long>(b) << 32 | a, own);
+}
 
 // Relaxation rates pre-broadcast to both lanes, built on the host:
 // D3Q27 omega, -omega, 1 - omega (divided by 216 for the kernels that fold
@@ -290,6 +305,7 @@ __global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const Ste
             v = Storage<T>::load(io.in[q] + R.off[j][k] + xs[i]);
         f[q] = Storage<T>::kScaled ? v * float(weight<Q>(q)) : v;
     }
+    const unsigned seed = cell_seed<Q>(f, R.own + x);
     float Fx, Fy, Fz;
     const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
     cell_force(a, dense_index(a.g, x, y, z), N, Fx, Fy, Fz);
@@ -297,7 +313,7 @@ __global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const Ste
     collide<Q>(f, Fx, Fy, Fz, r, a.has_force != 0);
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
-        store_dev_step<Q, T, q>(io.out[q] + R.own + x, f[q], sr_salt(R.own + x));
+        store_dev_step<Q, T, q>(io.out[q] + R.own + x, f[q], seed);
     });
 }
 
@@ -342,6 +358,7 @@ __global__ void __launch_bounds__(128, kStep2Blocks<T>) step2_kernel(const StepI
         }
         f[q] = v;  // weight-scaled 16-bit values go in as stored (collide27_g)
     }
+    const unsigned seed = pair_seed<27>(f, R.own + x0);
     f2 Fx, Fy, Fz;
     if (a.Ffield) {
         const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
@@ -360,7 +377,7 @@ __global__ void __launch_bounds__(128, kStep2Blocks<T>) step2_kernel(const StepI
         constexpr int q = decltype(iq)::value;
         constexpr float sc = store_scale<27, T>(q);
         const f2 v = sc == 1.0f ? f[q] : f[q] * f2(sc);
-        Pair<T>::template st2s<q>(io.out[q] + R.own + x0, v, sr_salt(R.own + x0));
+        Pair<T>::template st2s<q>(io.out[q] + R.own + x0, v, seed);
     });
 }
 
@@ -400,6 +417,7 @@ __global__ void __launch_bounds__(128, kQ15Blocks<T>) step2_q15_kernel(const Ste
         const f2 v = pull_pair<15, T, kWalls>(io, R, q, x0, xm, xp);
         f[q] = Storage<T>::kScaled ? v * f2(float(weight<15>(q))) : v;
     });
+    const unsigned seed = pair_seed<15>(f, R.own + x0);
     f2 Fx, Fy, Fz;
     if (a.Ffield) {
         const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
@@ -419,7 +437,7 @@ __global__ void __launch_bounds__(128, kQ15Blocks<T>) step2_q15_kernel(const Ste
     static_for<15>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
         const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<15>(q))) : f[q];
-        Pair<T>::template st2s<q>(io.out[q] + R.own + x0, v, sr_salt(R.own + x0));
+        Pair<T>::template st2s<q>(io.out[q] + R.own + x0, v, seed);
     });
 }
 
@@ -488,6 +506,7 @@ __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const 
         const f2 v = Pair<T>::ld2(io.in[q] + own);
         f[q] = sc == 1.0f ? v : v * f2(sc);
     });
+    const unsigned seed = pair_seed<Q>(f, own);
     f2 Fx, Fy, Fz;
     pair_force(a, x0, y, z, Fx, Fy, Fz);
     PairCollide<Q>::template run<kFoldedLoad<Q, T>()>(f, Fx, Fy, Fz, pr, a.has_force != 0);
@@ -495,7 +514,7 @@ __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const 
         constexpr int q = decltype(iq)::value;
         constexpr float sc = store_scale<Q, T>(q);
         const f2 v = sc == 1.0f ? f[q] : f[q] * f2(sc);
-        Pair<T>::template st2s<q>(io.out[opposite<Q>(q)] + own, v, sr_salt(own));
+        Pair<T>::template st2s<q>(io.out[opposite<Q>(q)] + own, v, seed);
     });
 }
 
@@ -536,6 +555,7 @@ __global__ void __launch_bounds__(128, (kAAOddBlocks<Q, T>))
         constexpr float sc = load_scale<Q, T>(q);
         f[q] = sc == 1.0f ? v : v * f2(sc);
     });
+    const unsigned seed = pair_seed<Q>(f, own);
     f2 Fx, Fy, Fz;
     pair_force(a, x0, y, z, Fx, Fy, Fz);
     PairCollide<Q>::template run<kFoldedLoad<Q, T>()>(f, Fx, Fy, Fz, pr, a.has_force != 0);
@@ -546,17 +566,16 @@ __global__ void __launch_bounds__(128, (kAAOddBlocks<Q, T>))
         constexpr float sc = store_scale<Q, T>(q);
         const f2 v = sc == 1.0f ? f[q] : f[q] * f2(sc);
         // downstream neighbour x + e_q: the row of the mirrored pull
-        const unsigned salt = sr_salt(own);
         if (kWalls && R.wall[2 - j][2 - k]) {
-            Pair<T>::template st2s<q>(io.out[o] + own, v, salt);
+            Pair<T>::template st2s<q>(io.out[o] + own, v, seed);
         } else {
             T *row = io.out[q] + R.off[2 - j][2 - k];
             if constexpr (i == 0)
-                Pair<T>::template st2s<q>(row + x0, v, salt);
+                Pair<T>::template st2s<q>(row + x0, v, seed);
             else if constexpr (i == 1)
-                Pair<T>::template st1x2s<q>(row + x0 + 1, row + xp, v, salt);
+                Pair<T>::template st1x2s<q>(row + x0 + 1, row + xp, v, seed);
             else
-                Pair<T>::template st1x2s<q>(row + xm, row + x0, v, salt);
+                Pair<T>::template st1x2s<q>(row + xm, row + x0, v, seed);
         }
     });
 }

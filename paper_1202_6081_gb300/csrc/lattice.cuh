@@ -139,28 +139,36 @@ struct Storage<__nv_bfloat16> {
 // Taylor-Green flow drifts to 1.5e-3 relative error of u in 500 steps that
 // way; a dither fixed per cell drifts the same way, so the random bits must
 // change as the values do).  The conversions are sm_100-class
-// cvt.rs.{f16x2,bf16x2}.f32, fed 32 random bits.  The bits are a hash of the
-// two values being rounded, of the cell pair's position and of the
-// population, so the rounding is a fixed function of the state: a step
+// cvt.rs.{f16x2,bf16x2}.f32, fed 32 random bits.  Each thread draws one seed
+// per step (sr_seed below): a mixing hash of the raw bits of a few of its
+// pre-collision values and of its position.  The bits of population q are
+// the seed XORed with a distinct constant, one logic operation per stored
+// pair of values.  So the rounding is a fixed function of the state: a step
 // recomputed from the same state (checkpointing) and the in-place scheme
-// round exactly as the two-buffer step does.
+// round exactly as the two-buffer step does; and the bits change from step
+// to step as the values move.
 
-// Salt of the cell (pair) at element offset own.
-__device__ __forceinline__ unsigned sr_salt(int own) { return static_cast<unsigned>(own); }
+// Two multiply-xorshift rounds: every output bit depends on every input bit.
+__device__ __forceinline__ unsigned sr_mix(unsigned x) {
+    x *= 0x9E3779B1u;
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    return x;
+}
 
-// 32 random bits for population q from (lo, hi, salt): one multiply-xorshift
-// round on the XOR of the inputs (hi rotated by 16), with a distinct odd
-// multiplier per population.  Each lane's conversion reads 13 (FP16) or 16
-// (BF16) bits; the low lane's bits mix its own discarded bits with the other
-// lane's and the salt's through the product's high half, the high lane's
-// are its discarded bits plus a product of everything below them, so given
-// the bits being rounded away the random bits stay uniform.
+// Seed from 64 bits of pre-collision values (the XOR of some of them) and the
+// element offset of the thread's cell (pair).
+__device__ __forceinline__ unsigned sr_seed(unsigned long long vals, int own) {
+    const unsigned lo = static_cast<unsigned>(vals), hi = static_cast<unsigned>(vals >> 32);
+    return sr_mix(lo ^ __funnelshift_l(hi, hi, 16) ^ static_cast<unsigned>(own));
+}
+
+// 32 random bits for population q: the FP16 conversion reads bits 0-12 for
+// the low lane and 16-28 for the high lane, BF16 bits 0-15 and 16-31.
 template <int q>
-__device__ __forceinline__ unsigned sr_bits(float lo, float hi, unsigned salt) {
-    constexpr unsigned kMul = 0x9E3779B1u + 2u * 0x2545F491u * static_cast<unsigned>(q);
-    const unsigned h = __float_as_uint(hi);
-    unsigned x = (__float_as_uint(lo) ^ __funnelshift_l(h, h, 16) ^ salt) * kMul;
-    return x ^ (x >> 16);
+__device__ __forceinline__ unsigned sr_bits(unsigned seed) {
+    return seed ^ (0x9E3779B9u * static_cast<unsigned>(q + 1));
 }
 
 // (lo, hi) -> packed 16-bit pair (lo in the low half), stochastically rounded.
@@ -183,8 +191,8 @@ struct PackSR<__nv_bfloat16> {
     }
 };
 template <typename T, int q>
-__device__ __forceinline__ unsigned pack_sr(float lo, float hi, unsigned salt) {
-    return PackSR<T>::run(lo, hi, sr_bits<q>(lo, hi, salt));
+__device__ __forceinline__ unsigned pack_sr(float lo, float hi, unsigned seed) {
+    return PackSR<T>::run(lo, hi, sr_bits<q>(seed));
 }
 
 // Deviation f - w (FP32) -> stored value.
@@ -199,9 +207,9 @@ __device__ __forceinline__ void store_dev(T *p, int a, float dev) {
 // The step's store of population a of one cell: FP32 as is, 16-bit
 // stochastically rounded.
 template <int Q, typename T, int a>
-__device__ __forceinline__ void store_dev_step(T *p, float dev, unsigned salt) {
+__device__ __forceinline__ void store_dev_step(T *p, float dev, unsigned seed) {
     if constexpr (Storage<T>::kScaled) {
-        const unsigned d = pack_sr<T, a>(dev * float(1.0 / weight<Q>(a)), 0.0f, salt);
+        const unsigned d = pack_sr<T, a>(dev * float(1.0 / weight<Q>(a)), 0.0f, seed);
         __stcs(reinterpret_cast<unsigned short *>(p), static_cast<unsigned short>(d & 0xffffu));
     } else {
         Storage<T>::store(p, dev);
