@@ -31,8 +31,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "D3Q27 fused step MLUPS and % of HBM roofline; adjoint/forward step-time ratio"
 UNIT = "MLUPS"
-BYTES_PER_CELL = {("q27", "f32"): 216, ("q27", "f16"): 108, ("q27", "bf16"): 108,
-                  ("q15", "f32"): 120, ("q15", "f16"): 60, ("q15", "bf16"): 60}
+# algorithmic bytes per cell update: every population read once and written
+# once; BF16 adds its momentum references (a float4 per pair of cells, 8 B
+# written and 8 B read per cell)
+BYTES_PER_CELL = {("q27", "f32"): 216, ("q27", "f16"): 108, ("q27", "bf16"): 124,
+                  ("q15", "f32"): 120, ("q15", "f16"): 60, ("q15", "bf16"): 76}
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth (a copy reaches ~86 % of it)
 KERNEL_SOURCES = ["lattice.cuh", "vec2.cuh", "collide_q27.cuh", "kernels.cuh"]
@@ -520,7 +523,7 @@ def run_ours(args):
         for st in ("f32", "f16", "bf16"):
             S, _, _ = make_solver(lbm, 15, size, st, 0.6)
             t = time_steps(torch, S, 200, 5)
-            bpc = (4 if st == "f32" else 2) * 2 * 15
+            bpc = BYTES_PER_CELL[("q15", st)]
             q15[st] = {"mlups": cells * 200 / t / 1e6, "GB/s": bpc * cells * 200 / t / 1e9,
                        "frac": bpc * cells * 200 / t / 1e9 / peak}
             del S

@@ -62,7 +62,13 @@ typedef enum { LBM_D3Q15 = 15, LBM_D3Q27 = 27 } lbm_lattice;
  * keep (f - w_a) / w_a in FP16 or BF16, stochastically rounded by the step
  * (up or down with probability proportional to the distance, from bits
  * hashed out of the values and the cell, so a recomputed step rounds the
- * same way) and rounded to nearest when a state is loaded. */
+ * same way) and rounded to nearest when a state is loaded.  BF16 (8
+ * significant bits) stores the populations with one or two nonzero velocity
+ * components relative to the linear part of the local equilibrium:
+ * (f_a - w_a) / w_a - e_a . J, with J = 3 times the mean velocity of the pair
+ * of cells (x even, x + 1) whose collision produced the value; J of every
+ * pair is kept in FP32 after the population planes (8 bytes per cell), so
+ * a BF16 state buffer is self-contained (see lbm_state_bytes). */
 typedef enum { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2 } lbm_storage;
 
 typedef enum {
@@ -97,6 +103,19 @@ typedef enum {
  * states). */
 #define LBM_INPLACE 4u
 
+/* bc_flags of lbm_create: stochastically rounded FP32 update (FP32 storage
+ * only; not with LBM_INPLACE).  Each step computes the collision's change
+ * d = f~ - f and stores f + d rounded up or down to FP32 with probability
+ * proportional to the distance (the exact sum from an error-free two-sum),
+ * instead of to nearest.  Meant for long runs to a steady state on small
+ * grids: there round-to-nearest makes the same rounding error at every step
+ * and those errors add up in the slowest modes (the grid-convergence study
+ * of Sec. 9 stops converging near 3e-4 relative error in FP32); with this
+ * flag they average out.  The rounding is a fixed function of the state.
+ * It runs the one-cell-per-thread kernel and costs throughput; not in the
+ * paper. */
+#define LBM_F32_SR 8u
+
 typedef struct lbm_ctx lbm_ctx;
 
 /* Create a solver context for one grid.
@@ -111,7 +130,8 @@ typedef struct lbm_ctx lbm_ctx;
  *   force    host, 3 values: the uniform body force F (lattice units); used
  *            when no force field is bound.  NULL means zero.
  *   bc_flags OR of LBM_WALL_Y / LBM_WALL_Z (0: fully periodic), optionally
- *            with LBM_INPLACE (then nx must be even).
+ *            with LBM_INPLACE (then nx must be even) or LBM_F32_SR (then
+ *            storage must be LBM_STORE_F32, and not LBM_INPLACE).
  *   storage  an lbm_storage value.
  *   out      receives the context (set to NULL on error).
  * Errors: LBM_EINVAL, LBM_ENOMEM (context allocation), LBM_ECUDA (no usable
@@ -127,7 +147,11 @@ void lbm_destroy(lbm_ctx *ctx);
 
 /* Size in bytes of each of the two state buffers the caller must provide:
  * Q populations of ny * nz rows of a row pitch >= nx elements (a multiple of
- * 32 elements), in the storage type.  0 for a NULL context. */
+ * 32 elements), in the storage type; for LBM_STORE_BF16 followed by the
+ * momentum references (one float4 per pair of cells of the pitched rows,
+ * 8 bytes per cell; two such arrays with LBM_INPLACE).  A state is fully
+ * described by these bytes: copying them copies the state.  0 for a NULL
+ * context. */
 size_t lbm_state_bytes(const lbm_ctx *ctx);
 
 /* Row pitch in elements of the state buffers (see lbm_state_bytes). */

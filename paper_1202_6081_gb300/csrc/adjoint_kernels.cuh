@@ -70,11 +70,15 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const StepIO<T> io, const 
     for (int q = 0; q < Q; ++q) {
         const int i = ex<Q>(q) + 1, j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
         // state at t: pull from x - e_q
-        float v;
-        if (kWalls && R.wall[j][k])
-            v = Storage<T>::load(io.in[opposite<Q>(q)] + R.own + x);
-        else
-            v = Storage<T>::load(io.in[q] + R.off[j][k] + xs[i]);
+        const bool wall = kWalls && R.wall[j][k];
+        const int src = wall ? R.own + x : R.off[j][k] + xs[i];
+        const T *plane = wall ? io.in[opposite<Q>(q)] : io.in[q];
+        float v = Storage<T>::load(plane + src);
+        if (Storage<T>::kRef && has_ref<Q>(q)) {  // BF16 momentum reference (lattice.cuh)
+            const float4 J = __ldg(io.ref_in + (src >> 1));
+            const float r = ex<Q>(q) * J.x + ey<Q>(q) * J.y + ez<Q>(q) * J.z;
+            v += wall ? -r : r;
+        }
         f[q] = Storage<T>::kScaled ? v * float(weight<Q>(q)) : v;
         // adjoint at t+1: from x + e_q (the mirrored pull)
         if (kWalls && R.wall[2 - j][2 - k])
@@ -123,8 +127,7 @@ __global__ void __launch_bounds__(128, 3) adjoint2_kernel(const StepIO<T> io, co
         constexpr int q = decltype(iq)::value;
         constexpr int i = ex<Q>(q), j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
         constexpr int o = opposite<Q>(q);
-        const f2 v = pull_pair<Q, T, kWalls>(io, R, q, x0, xm, xp);
-        f[q] = Storage<T>::kScaled ? v * f2(float(weight<Q>(q))) : v;
+        f[q] = pull_pair<Q, T, kWalls>(io, R, q, x0, xm, xp);
         if (kWalls && R.wall[2 - j][2 - k]) {
             mu[q] = Pair<float>::ld2(g.lam_next[o] + own);
         } else {
@@ -137,6 +140,14 @@ __global__ void __launch_bounds__(128, 3) adjoint2_kernel(const StepIO<T> io, co
                 mu[q] = f2(__ldg(row + xm), __ldg(row + x0));
         }
     });
+    // deviations f - w: BF16 references added, 16-bit values scaled by w
+    if constexpr (Storage<T>::kRef) add_refs_pair<Q, kWalls>(io.ref_in, R, x0, xm, xp, f);
+    if constexpr (Storage<T>::kScaled) {
+        static_for<Q>([&](auto iq) {
+            constexpr int q = decltype(iq)::value;
+            f[q] = f[q] * f2(float(weight<Q>(q)));
+        });
+    }
     const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
     const long long c = dense_index(a.g, x0, y, z);
     f2 Fx, Fy, Fz;
@@ -291,6 +302,7 @@ cudaError_t launch_adjoint(const void *f_t, const float *lam_next, float *lam_ou
         g.lam_next[q] = lam_next + q * a.g.pop;
         g.lam_out[q] = lam_out + q * a.g.pop;
     }
+    io.ref_in = Storage<T>::kRef ? ref_array<Q>(static_cast<const T *>(f_t), a.g.pop, 0) : nullptr;
     g.gF = gF;
     if (a.g.nx % 2 == 0) {
         Grid half = a.g;

@@ -46,6 +46,7 @@ struct lbm_ctx {
     bool bound;
     bool state_set;
     bool inplace;  // single-buffer (AA) streaming; g.layout tracks the state's layout
+    bool sr32;     // stochastically rounded FP32 update (LBM_F32_SR)
     int device;
     int graph_steps;          // steps per captured graph; 0: launch each step
     cudaStream_t cap_stream;  // private stream the graphs are captured on
@@ -69,6 +70,7 @@ lbm::StepArgs step_args(const lbm_ctx *c) {
     for (int i = 0; i < 3; ++i) a.F[i] = c->F[i];
     a.Ffield = c->Ffield;
     a.has_force = (c->Ffield || c->F[0] != 0.0f || c->F[1] != 0.0f || c->F[2] != 0.0f) ? 1 : 0;
+    a.sr32 = c->sr32 ? 1 : 0;
     return a;
 }
 
@@ -217,8 +219,10 @@ lbm_status lbm_create(lbm_lattice lattice, int nx, int ny, int nz, const double 
     if (Q != 27 && Q != 15) return LBM_EINVAL;
     if (nx < 1 || ny < 1 || nz < 1) return LBM_EINVAL;
     if (ny > 65535 || nz > 65535) return LBM_EINVAL;  // launch grid limits (y, z)
-    if (bc_flags & ~(LBM_WALL_Y | LBM_WALL_Z | LBM_INPLACE)) return LBM_EINVAL;
+    if (bc_flags & ~(LBM_WALL_Y | LBM_WALL_Z | LBM_INPLACE | LBM_F32_SR)) return LBM_EINVAL;
     const bool inplace = (bc_flags & LBM_INPLACE) != 0;
+    const bool sr32 = (bc_flags & LBM_F32_SR) != 0;
+    if (sr32 && (inplace || storage != LBM_STORE_F32)) return LBM_EINVAL;
     if (inplace && (nx % 2) != 0) return LBM_EINVAL;  // the in-place kernels take cell pairs
     if (storage != LBM_STORE_F32 && storage != LBM_STORE_F16 && storage != LBM_STORE_BF16)
         return LBM_EINVAL;
@@ -243,6 +247,7 @@ lbm_status lbm_create(lbm_lattice lattice, int nx, int ny, int nz, const double 
     c->g.bc = bc_flags & (LBM_WALL_Y | LBM_WALL_Z);
     c->g.layout = inplace ? lbm::kAANatural : lbm::kPull;
     c->inplace = inplace;
+    c->sr32 = sr32;
     c->g.plane = px * ny;
     c->g.pop = px * ny * nz;
     for (int b = 0; b < 27; ++b) c->w[b] = (b >= 4 && b < Q) ? float(omega[b]) : 0.0f;
@@ -265,7 +270,11 @@ void lbm_destroy(lbm_ctx *c) {
 
 size_t lbm_state_bytes(const lbm_ctx *c) {
     if (!c) return 0;
-    return size_t(c->Q) * size_t(c->g.pop) * elem_bytes(c->storage);
+    size_t bytes = size_t(c->Q) * size_t(c->g.pop) * elem_bytes(c->storage);
+    // BF16: the momentum references of the stored values, a float4 per pair
+    // of cells (8 bytes per cell), two arrays for the in-place scheme
+    if (c->storage == LBM_STORE_BF16) bytes += (c->inplace ? 2 : 1) * 8 * size_t(c->g.pop);
+    return bytes;
 }
 
 int lbm_row_pitch(const lbm_ctx *c) { return c ? c->g.px : 0; }

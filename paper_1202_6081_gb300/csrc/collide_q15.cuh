@@ -334,10 +334,11 @@ __device__ __forceinline__ void update15(V (&f)[15], const V (&g)[15], const V (
 // One cell (or a pair, V = f2): deviations in, post-collision deviations
 // out.  with_source = false (no force anywhere) takes the force-free cascade
 // and skips S.
+// u_out: the velocity (with the F/2 shift).
 template <typename V>
 __device__ __forceinline__ void collide15(V (&f)[15], V Fx, V Fy, V Fz, const Rates15<V> &r,
-                                          bool with_source) {
-    V g[15], ux, uy, uz;
+                                          bool with_source, V &ux, V &uy, V &uz) {
+    V g[15];
     V m[15];
     if (with_source) {
         kernels15(f, Fx, Fy, Fz, r, ux, uy, uz, g);
@@ -346,6 +347,30 @@ __device__ __forceinline__ void collide15(V (&f)[15], V Fx, V Fy, V Fz, const Ra
     } else {
         kernels15_unforced(f, r, ux, uy, uz, g);
         update15<V, false>(f, g, m);
+    }
+}
+template <typename V>
+__device__ __forceinline__ void collide15(V (&f)[15], V Fx, V Fy, V Fz, const Rates15<V> &r,
+                                          bool with_source) {
+    V ux, uy, uz;
+    collide15<V>(f, Fx, Fy, Fz, r, with_source, ux, uy, uz);
+}
+
+// The change the collision makes, d = K.g + S (Eq. cascadedcollision1), for
+// the incremental update f~ = f + d: the update applied to zeros.
+__device__ __forceinline__ void collide15_delta(const float (&f)[15], float Fx, float Fy,
+                                                float Fz, const Rates15<float> &r, bool with_source,
+                                                float (&d)[15]) {
+    float g[15], m[15], ux, uy, uz;
+#pragma unroll
+    for (int a = 0; a < 15; ++a) d[a] = 0.0f;
+    if (with_source) {
+        kernels15(f, Fx, Fy, Fz, r, ux, uy, uz, g);
+        source_projections15(Fx, Fy, Fz, ux, uy, uz, m);
+        update15<float, true>(d, g, m);
+    } else {
+        kernels15_unforced(f, r, ux, uy, uz, g);
+        update15<float, false>(d, g, m);
     }
 }
 

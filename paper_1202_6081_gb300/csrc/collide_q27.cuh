@@ -390,10 +390,12 @@ __device__ __forceinline__ void forward27_w(const V (&s)[27], V (&D)[3][3][3], V
 // The collision of collide27 with outputs G_i G_j G_k f~ (see (1) above);
 // kWeighted: inputs are weight-scaled values s and r.omw holds
 // (1 - omega) / 216 (see (2) above).
+// u_out: the velocity (with the F/2 shift) of Eq. velocitycalculation.
 template <typename V, bool kWeighted>
-__device__ __forceinline__ void collide27_g(V (&f)[27], V Fx, V Fy, V Fz, const Rates27<V> &r) {
+__device__ __forceinline__ void collide27_g(V (&f)[27], V Fx, V Fy, V Fz, const Rates27<V> &r,
+                                            V &ux, V &uy, V &uz) {
     V D[3][3][3];
-    V drho, ux, uy, uz;
+    V drho;
     if constexpr (kWeighted)
         forward27_w(f, D, Fx, Fy, Fz, drho, ux, uy, uz);
     else
@@ -404,13 +406,19 @@ __device__ __forceinline__ void collide27_g(V (&f)[27], V Fx, V Fy, V Fz, const 
     relax27(D, ux, uy, uz, drho, r);
     inverse27_g(D, ux, uy, uz, f);
 }
+template <typename V, bool kWeighted>
+__device__ __forceinline__ void collide27_g(V (&f)[27], V Fx, V Fy, V Fz, const Rates27<V> &r) {
+    V ux, uy, uz;
+    collide27_g<V, kWeighted>(f, Fx, Fy, Fz, r, ux, uy, uz);
+}
 
 // One cell (or a pair of cells, V = f2): pre-collision deviations in,
 // post-collision deviations out (both f - w, slot order).
 template <typename V>
-__device__ __forceinline__ void collide27(V (&f)[27], V Fx, V Fy, V Fz, const Rates27<V> &r) {
+__device__ __forceinline__ void collide27(V (&f)[27], V Fx, V Fy, V Fz, const Rates27<V> &r,
+                                          V &ux, V &uy, V &uz) {
     V D[3][3][3];
-    V drho, ux, uy, uz;
+    V drho;
     forward27(f, D, Fx, Fy, Fz, drho, ux, uy, uz);
     // The sweeps produced the central moments of the deviations; those of
     // the rest state are handled in closed form inside relax27, so D is
@@ -421,6 +429,39 @@ __device__ __forceinline__ void collide27(V (&f)[27], V Fx, V Fy, V Fz, const Ra
     D[0][0][1] = D[0][0][1] + Fz;
     relax27(D, ux, uy, uz, drho, r);
     inverse27(D, ux, uy, uz, f);
+}
+template <typename V>
+__device__ __forceinline__ void collide27(V (&f)[27], V Fx, V Fy, V Fz, const Rates27<V> &r) {
+    V ux, uy, uz;
+    collide27<V>(f, Fx, Fy, Fz, r, ux, uy, uz);
+}
+
+// The change the collision makes, d = f~ - f (source included), for the
+// incremental update f~ = f + d: the inverse transform is linear in the
+// moments for a given u, and maps the pre-collision moments back to f, so
+// d = Inv(D~ - D) with D the pre-collision moments (before the source).
+__device__ __forceinline__ void collide27_delta(const float (&f)[27], float Fx, float Fy, float Fz,
+                                                const Rates27<float> &r, float (&d)[27]) {
+    float D[3][3][3], D0[3][3][3];
+    float drho, ux, uy, uz;
+    forward27(f, D, Fx, Fy, Fz, drho, ux, uy, uz);
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int n = 0; n < 3; ++n)
+#pragma unroll
+            for (int p = 0; p < 3; ++p) D0[m][n][p] = D[m][n][p];
+    D[1][0][0] = D[1][0][0] + Fx;
+    D[0][1][0] = D[0][1][0] + Fy;
+    D[0][0][1] = D[0][0][1] + Fz;
+    relax27(D, ux, uy, uz, drho, r);
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int n = 0; n < 3; ++n)
+#pragma unroll
+            for (int p = 0; p < 3; ++p) D[m][n][p] = D[m][n][p] - D0[m][n][p];
+    inverse27(D, ux, uy, uz, d);
 }
 
 // Deviations of the initial state f = f^at(rho, u) - S/2 at one cell

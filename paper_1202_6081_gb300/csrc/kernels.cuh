@@ -19,6 +19,7 @@ struct StepArgs {
     float F[3];            // uniform body force
     const float *Ffield;   // per-cell force [3][nz][ny][nx] or nullptr
     int has_force;         // 0: no force anywhere (the source term vanishes)
+    int sr32;              // FP32 storage: incremental update, stochastically rounded
 };
 
 // Launch geometry shared by the per-cell kernels (cell_launch below).
@@ -107,6 +108,42 @@ __device__ __forceinline__ void collide<15>(float (&f)[15], float Fx, float Fy, 
     collide15<float>(f, Fx, Fy, Fz, r, has_force);
 }
 
+// The same, returning the cell's velocity (Eq. velocitycalculation).
+template <int Q>
+__device__ __forceinline__ void collide_u(float (&f)[Q], float Fx, float Fy, float Fz,
+                                          const typename Rates<Q>::type &r, bool has_force,
+                                          float &ux, float &uy, float &uz);
+template <>
+__device__ __forceinline__ void collide_u<27>(float (&f)[27], float Fx, float Fy, float Fz,
+                                              const Rates27<float> &r, bool, float &ux, float &uy,
+                                              float &uz) {
+    collide27<float>(f, Fx, Fy, Fz, r, ux, uy, uz);
+}
+template <>
+__device__ __forceinline__ void collide_u<15>(float (&f)[15], float Fx, float Fy, float Fz,
+                                              const Rates15<float> &r, bool has_force, float &ux,
+                                              float &uy, float &uz) {
+    collide15<float>(f, Fx, Fy, Fz, r, has_force, ux, uy, uz);
+}
+
+// The change d = f~ - f the collision makes (for the incremental update).
+template <int Q>
+__device__ __forceinline__ void collide_delta(const float (&f)[Q], float Fx, float Fy, float Fz,
+                                              const typename Rates<Q>::type &r, bool has_force,
+                                              float (&d)[Q]);
+template <>
+__device__ __forceinline__ void collide_delta<27>(const float (&f)[27], float Fx, float Fy,
+                                                  float Fz, const Rates27<float> &r, bool,
+                                                  float (&d)[27]) {
+    collide27_delta(f, Fx, Fy, Fz, r, d);
+}
+template <>
+__device__ __forceinline__ void collide_delta<15>(const float (&f)[15], float Fx, float Fy,
+                                                  float Fz, const Rates15<float> &r,
+                                                  bool has_force, float (&d)[15]) {
+    collide15_delta(f, Fx, Fy, Fz, r, has_force, d);
+}
+
 template <int Q>
 __device__ __forceinline__ void equilibrium(float drho, float ux, float uy, float uz, float Fx,
                                             float Fy, float Fz, float (&f)[Q]);
@@ -142,6 +179,8 @@ template <typename T>
 struct StepIO {
     const T *in[27];
     T *out[27];
+    const float4 *ref_in;  // momentum references of the input state (BF16), else unused
+    float4 *ref_out;       // and of the output state
 };
 
 // 2-cell pair helpers for the packed kernel (x0 even, row pitch even).
@@ -286,34 +325,125 @@ __device__ __forceinline__ Rows<kWalls> pull_rows(const Grid &g, int y, int z) {
     return r;
 }
 
+// BF16 momentum references (see lattice.cuh) for the pair kernels.
+//
+// Reader: adds to the pulled raw values f[q] of cells (x0, x0 + 1) the
+// reference of each value's producer: for e_x = 0 both from the pair of the
+// source row, for e_x = +1 from the pairs of x0 - 1 and x0, for e_x = -1 of
+// x0 + 1 and x0 + 2; behind a wall minus that of the own pair.
+template <int Q, bool kWalls>
+__device__ __forceinline__ void add_refs_pair(const float4 *__restrict__ ref, const Rows<kWalls> &R,
+                                              int x0, int xm, int xp, f2 (&f)[Q]) {
+    static_for<Q>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        if constexpr (has_ref<Q>(q)) {
+            constexpr int i = ex<Q>(q), j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
+            float rlo, rhi;
+            if (kWalls && R.wall[j][k]) {
+                rlo = rhi = -ref_dot<Q, q>(__ldg(ref + ((R.own + x0) >> 1)));
+            } else {
+                const float4 *row = ref + (R.off[j][k] >> 1);
+                const float4 C = __ldg(row + (x0 >> 1));
+                if constexpr (i == 0) {
+                    rlo = rhi = ref_dot<Q, q>(C);
+                } else if constexpr (i == 1) {
+                    rlo = ref_dot<Q, q>(__ldg(row + (xm >> 1)));
+                    rhi = ref_dot<Q, q>(C);
+                } else {
+                    rlo = ref_dot<Q, q>(C);
+                    rhi = ref_dot<Q, q>(__ldg(row + (xp >> 1)));
+                }
+            }
+            f[q] = f[q] + f2(rlo, rhi);
+        }
+    });
+}
+
+// Writer: the pair's reference J = 3 u-bar (mean velocity of the two cells).
+__device__ __forceinline__ float4 pair_ref(f2 ux, f2 uy, f2 uz) {
+    return make_float4(1.5f * (ux.lo() + ux.hi()), 1.5f * (uy.lo() + uy.hi()),
+                       1.5f * (uz.lo() + uz.hi()), 0.0f);
+}
+
+// Stored value of population q of a pair from its post-collision value v
+// times the store scale sc: v sc, minus e_q . J for the referenced
+// populations of BF16 storage.
+template <int Q, typename T, int q>
+__device__ __forceinline__ f2 stored_pair(f2 v, float sc, const float4 &J) {
+    if constexpr (Storage<T>::kRef && has_ref<Q>(q))
+        return vfma(v, f2(sc), f2(-ref_dot<Q, q>(J)));
+    else
+        return sc == 1.0f ? v : v * f2(sc);
+}
+
 // One fused step, one cell per thread: pull-gather (streaming with
-// bounce-back), collision, store.
-template <int Q, typename T, bool kWalls>
+// bounce-back), collision, store.  With BF16 momentum references the cells
+// x (even) and x + 1, held by neighbouring lanes, exchange their velocities
+// for the pair's reference, so every lane takes part: cells beyond the grid
+// edge compute on a clamped cell and store nothing.
+// kSR (FP32 storage, opt-in): the update is f~ = f + d with d the
+// collision's change, and that last addition is rounded stochastically
+// (add_sr32), so that no rounding error repeats identically step after step
+// at a steady state.
+template <int Q, typename T, bool kWalls, bool kSR = false>
 __global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const StepArgs a) {
     int x, y, z;
-    if (!cell_coords(a.g, x, y, z)) return;
+    const bool inside = cell_coords(a.g, x, y, z);
+    if constexpr (Storage<T>::kRef) {
+        x = min(x, a.g.nx - 1);
+        y = min(y, a.g.ny - 1);
+    } else {
+        if (!inside) return;
+    }
     const Rows<kWalls> R = pull_rows<kWalls>(a.g, y, z);
     const int xs[3] = {(x + 1 == a.g.nx) ? 0 : x + 1, x, (x == 0) ? a.g.nx - 1 : x - 1};
     float f[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int i = ex<Q>(q) + 1, j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
-        float v;
-        if (kWalls && R.wall[j][k])
-            v = Storage<T>::load(io.in[opposite<Q>(q)] + R.own + x);
-        else
-            v = Storage<T>::load(io.in[q] + R.off[j][k] + xs[i]);
+    static_for<Q>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        constexpr int i = ex<Q>(q) + 1, j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
+        const bool wall = kWalls && R.wall[j][k];
+        const int src = wall ? R.own + x : R.off[j][k] + xs[i];
+        const T *plane = wall ? io.in[opposite<Q>(q)] : io.in[q];
+        float v = Storage<T>::load(plane + src);
+        if constexpr (Storage<T>::kRef && has_ref<Q>(q)) {
+            const float r = ref_dot<Q, q>(__ldg(io.ref_in + (src >> 1)));
+            v += wall ? -r : r;
+        }
         f[q] = Storage<T>::kScaled ? v * float(weight<Q>(q)) : v;
-    }
+    });
     const unsigned seed = cell_seed<Q>(f, R.own + x);
     float Fx, Fy, Fz;
     const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
     cell_force(a, dense_index(a.g, x, y, z), N, Fx, Fy, Fz);
     const typename Rates<Q>::type r = load_rates<Q>(a);
-    collide<Q>(f, Fx, Fy, Fz, r, a.has_force != 0);
+    float ux, uy, uz;
+    if constexpr (kSR) {
+        float d[Q];
+        collide_delta<Q>(f, Fx, Fy, Fz, r, a.has_force != 0, d);
+        static_for<Q>([&](auto iq) {
+            constexpr int q = decltype(iq)::value;
+            f[q] = add_sr32(f[q], d[q], sr_bits<q>(seed));
+        });
+    } else {
+        collide_u<Q>(f, Fx, Fy, Fz, r, a.has_force != 0, ux, uy, uz);
+    }
+    float4 J = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if constexpr (Storage<T>::kRef) {
+        const float px = __shfl_xor_sync(0xffffffffu, ux, 1);
+        const float py = __shfl_xor_sync(0xffffffffu, uy, 1);
+        const float pz = __shfl_xor_sync(0xffffffffu, uz, 1);
+        if ((x ^ 1) < a.g.nx)  // both cells of the pair exist (a + b == b + a exactly)
+            J = make_float4(1.5f * (ux + px), 1.5f * (uy + py), 1.5f * (uz + pz), 0.0f);
+        else
+            J = make_float4(3.0f * ux, 3.0f * uy, 3.0f * uz, 0.0f);
+        if (!inside) return;
+        if ((x & 1) == 0) __stcs(io.ref_out + ((R.own + x) >> 1), J);
+    }
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
-        store_dev_step<Q, T, q>(io.out[q] + R.own + x, f[q], seed);
+        float ref = 0.0f;
+        if constexpr (Storage<T>::kRef && has_ref<Q>(q)) ref = ref_dot<Q, q>(J);
+        store_dev_step<Q, T, q>(io.out[q] + R.own + x, f[q], seed, ref);
     });
 }
 
@@ -358,6 +488,7 @@ __global__ void __launch_bounds__(128, kStep2Blocks<T>) step2_kernel(const StepI
         }
         f[q] = v;  // weight-scaled 16-bit values go in as stored (collide27_g)
     }
+    if constexpr (Storage<T>::kRef) add_refs_pair<27, kWalls>(io.ref_in, R, x0, xm, xp, f);
     const unsigned seed = pair_seed<27>(f, R.own + x0);
     f2 Fx, Fy, Fz;
     if (a.Ffield) {
@@ -372,11 +503,16 @@ __global__ void __launch_bounds__(128, kStep2Blocks<T>) step2_kernel(const StepI
         Fz = f2(a.F[2]);
     }
     const Rates27<f2> r = load_rates_packed(pr);
-    collide27_g<f2, Storage<T>::kScaled>(f, Fx, Fy, Fz, r);
+    f2 ux, uy, uz;
+    collide27_g<f2, Storage<T>::kScaled>(f, Fx, Fy, Fz, r, ux, uy, uz);
+    float4 J = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if constexpr (Storage<T>::kRef) {
+        J = pair_ref(ux, uy, uz);
+        __stcs(io.ref_out + ((R.own + x0) >> 1), J);
+    }
     static_for<27>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
-        constexpr float sc = store_scale<27, T>(q);
-        const f2 v = sc == 1.0f ? f[q] : f[q] * f2(sc);
+        const f2 v = stored_pair<27, T, q>(f[q], store_scale<27, T>(q), J);
         Pair<T>::template st2s<q>(io.out[q] + R.own + x0, v, seed);
     });
 }
@@ -414,9 +550,15 @@ __global__ void __launch_bounds__(128, kQ15Blocks<T>) step2_q15_kernel(const Ste
     f2 f[15];
     static_for<15>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
-        const f2 v = pull_pair<15, T, kWalls>(io, R, q, x0, xm, xp);
-        f[q] = Storage<T>::kScaled ? v * f2(float(weight<15>(q))) : v;
+        f[q] = pull_pair<15, T, kWalls>(io, R, q, x0, xm, xp);
     });
+    if constexpr (Storage<T>::kRef) add_refs_pair<15, kWalls>(io.ref_in, R, x0, xm, xp, f);
+    if constexpr (Storage<T>::kScaled) {
+        static_for<15>([&](auto iq) {
+            constexpr int q = decltype(iq)::value;
+            f[q] = f[q] * f2(float(weight<15>(q)));
+        });
+    }
     const unsigned seed = pair_seed<15>(f, R.own + x0);
     f2 Fx, Fy, Fz;
     if (a.Ffield) {
@@ -433,10 +575,16 @@ __global__ void __launch_bounds__(128, kQ15Blocks<T>) step2_q15_kernel(const Ste
     Rates15<f2> r;
 #pragma unroll
     for (int b = 0; b < 15; ++b) r.w[b] = f2(pr.w15[b]);
-    collide15<f2>(f, Fx, Fy, Fz, r, a.has_force != 0);
+    f2 ux, uy, uz;
+    collide15<f2>(f, Fx, Fy, Fz, r, a.has_force != 0, ux, uy, uz);
+    float4 J = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if constexpr (Storage<T>::kRef) {
+        J = pair_ref(ux, uy, uz);
+        __stcs(io.ref_out + ((R.own + x0) >> 1), J);
+    }
     static_for<15>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
-        const f2 v = Storage<T>::kScaled ? f[q] * f2(float(1.0 / weight<15>(q))) : f[q];
+        const f2 v = stored_pair<15, T, q>(f[q], store_scale<15, T>(q), J);
         Pair<T>::template st2s<q>(io.out[q] + R.own + x0, v, seed);
     });
 }
@@ -459,20 +607,22 @@ template <>
 struct PairCollide<27> {
     template <bool kWeighted>
     __device__ __forceinline__ static void run(f2 (&f)[27], f2 Fx, f2 Fy, f2 Fz,
-                                               const PackedRates &pr, bool) {
+                                               const PackedRates &pr, bool, f2 &ux, f2 &uy,
+                                               f2 &uz) {
         const Rates27<f2> r = load_rates_packed(pr);
-        collide27_g<f2, kWeighted>(f, Fx, Fy, Fz, r);
+        collide27_g<f2, kWeighted>(f, Fx, Fy, Fz, r, ux, uy, uz);
     }
 };
 template <>
 struct PairCollide<15> {
     template <bool>
     __device__ __forceinline__ static void run(f2 (&f)[15], f2 Fx, f2 Fy, f2 Fz,
-                                               const PackedRates &pr, bool has_force) {
+                                               const PackedRates &pr, bool has_force, f2 &ux,
+                                               f2 &uy, f2 &uz) {
         Rates15<f2> r;
 #pragma unroll
         for (int b = 0; b < 15; ++b) r.w[b] = f2(pr.w15[b]);
-        collide15<f2>(f, Fx, Fy, Fz, r, has_force);
+        collide15<f2>(f, Fx, Fy, Fz, r, has_force, ux, uy, uz);
     }
 };
 
@@ -491,29 +641,58 @@ __device__ __forceinline__ void pair_force(const StepArgs &a, int x0, int y, int
     }
 }
 
+// Raw pulled values -> the collision's inputs: BF16 references added (their
+// producers are the pull sources, see lattice.cuh), then the load scale.
+template <int Q, typename T, bool kWalls>
+__device__ __forceinline__ void pair_inputs(const StepIO<T> &io, const Rows<kWalls> &R, int x0,
+                                            int xm, int xp, f2 (&f)[Q]) {
+    if constexpr (Storage<T>::kRef) add_refs_pair<Q, kWalls>(io.ref_in, R, x0, xm, xp, f);
+    static_for<Q>([&](auto iq) {
+        constexpr int q = decltype(iq)::value;
+        constexpr float sc = load_scale<Q, T>(q);
+        if constexpr (sc != 1.0f) f[q] = f[q] * f2(sc);
+    });
+}
+
+// The collision of an in-place step, then the pair's reference (BF16).
 template <int Q, typename T>
+__device__ __forceinline__ float4 pair_collide(const StepIO<T> &io, const StepArgs &a,
+                                               const PackedRates &pr, int x0, int y, int z,
+                                               int own, f2 (&f)[Q]) {
+    f2 Fx, Fy, Fz, ux, uy, uz;
+    pair_force(a, x0, y, z, Fx, Fy, Fz);
+    PairCollide<Q>::template run<kFoldedLoad<Q, T>()>(f, Fx, Fy, Fz, pr, a.has_force != 0, ux,
+                                                      uy, uz);
+    float4 J = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if constexpr (Storage<T>::kRef) {
+        J = pair_ref(ux, uy, uz);
+        __stcs(io.ref_out + (own >> 1), J);
+    }
+    return J;
+}
+
+template <int Q, typename T, bool kWalls>
 __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const StepArgs a,
                                                       const PackedRates pr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
     const int x0 = 2 * t;
     if (x0 >= a.g.nx || y >= a.g.ny) return;
-    const int own = (z * a.g.ny + y) * a.g.px + x0;
+    const Rows<kWalls> R = pull_rows<kWalls>(a.g, y, z);  // producers of the values (BF16)
+    const int xm = (x0 == 0) ? a.g.nx - 1 : x0 - 1;
+    const int xp = (x0 + 2 == a.g.nx) ? 0 : x0 + 2;
+    const int own = R.own + x0;
     f2 f[Q];
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
-        constexpr float sc = load_scale<Q, T>(q);
-        const f2 v = Pair<T>::ld2(io.in[q] + own);
-        f[q] = sc == 1.0f ? v : v * f2(sc);
+        f[q] = Pair<T>::ld2(io.in[q] + own);
     });
+    pair_inputs<Q, T, kWalls>(io, R, x0, xm, xp, f);
     const unsigned seed = pair_seed<Q>(f, own);
-    f2 Fx, Fy, Fz;
-    pair_force(a, x0, y, z, Fx, Fy, Fz);
-    PairCollide<Q>::template run<kFoldedLoad<Q, T>()>(f, Fx, Fy, Fz, pr, a.has_force != 0);
+    const float4 J = pair_collide<Q, T>(io, a, pr, x0, y, z, own, f);
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
-        constexpr float sc = store_scale<Q, T>(q);
-        const f2 v = sc == 1.0f ? f[q] : f[q] * f2(sc);
+        const f2 v = stored_pair<Q, T, q>(f[q], store_scale<Q, T>(q), J);
         Pair<T>::template st2s<q>(io.out[opposite<Q>(q)] + own, v, seed);
     });
 }
@@ -552,19 +731,16 @@ __global__ void __launch_bounds__(128, (kAAOddBlocks<Q, T>))
             else
                 v = f2(Pair<T>::ld1(row + x0 + 1), Pair<T>::ld1(row + xp));
         }
-        constexpr float sc = load_scale<Q, T>(q);
-        f[q] = sc == 1.0f ? v : v * f2(sc);
+        f[q] = v;
     });
+    pair_inputs<Q, T, kWalls>(io, R, x0, xm, xp, f);
     const unsigned seed = pair_seed<Q>(f, own);
-    f2 Fx, Fy, Fz;
-    pair_force(a, x0, y, z, Fx, Fy, Fz);
-    PairCollide<Q>::template run<kFoldedLoad<Q, T>()>(f, Fx, Fy, Fz, pr, a.has_force != 0);
+    const float4 J = pair_collide<Q, T>(io, a, pr, x0, y, z, own, f);
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
         constexpr int i = ex<Q>(q), j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
         constexpr int o = opposite<Q>(q);
-        constexpr float sc = store_scale<Q, T>(q);
-        const f2 v = sc == 1.0f ? f[q] : f[q] * f2(sc);
+        const f2 v = stored_pair<Q, T, q>(f[q], store_scale<Q, T>(q), J);
         // downstream neighbour x + e_q: the row of the mirrored pull
         if (kWalls && R.wall[2 - j][2 - k]) {
             Pair<T>::template st2s<q>(io.out[o] + own, v, seed);
@@ -609,6 +785,44 @@ __global__ void __launch_bounds__(128) set_state_kernel(T *__restrict__ buf, con
 #pragma unroll
     for (int a = 0; a < Q; ++a) f[a] = float(fin[a * N + c] - weight<Q>(a));
     scatter_state<Q, T>(buf, g, pull_sources(g, x, y, z), f);
+}
+
+// BF16 momentum references of a state being loaded (reference array 0), one
+// thread per pair of cells: J = 3 x the mean velocity of the pair, from the
+// velocity field u when given, else from the momentum of the distributions
+// f (dense FP64 [Q][N]).  Any J would do as long as the values are stored
+// and read against the same one; this one keeps the stored values small.
+template <int Q, typename T>
+__global__ void __launch_bounds__(128) ref_init_kernel(T *__restrict__ buf, const Grid g,
+                                                       const double *__restrict__ u,
+                                                       const double *__restrict__ f) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    const int x0 = 2 * t;
+    if (x0 >= g.nx || y >= g.ny) return;
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    const long long c = dense_index(g, x0, y, z);
+    const int n = (x0 + 1 < g.nx) ? 2 : 1;
+    float v[2][3];
+    for (int m = 0; m < n; ++m)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double sum = 0.0;
+            if (u) {
+                sum = u[d * N + c + m];
+            } else {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const int e = d == 0 ? ex<Q>(q) : d == 1 ? ey<Q>(q) : ez<Q>(q);
+                    if (e) sum += e * f[q * N + c + m];
+                }
+            }
+            v[m][d] = float(sum);
+        }
+    const float4 J = n == 2 ? make_float4(1.5f * (v[0][0] + v[1][0]), 1.5f * (v[0][1] + v[1][1]),
+                                          1.5f * (v[0][2] + v[1][2]), 0.0f)
+                            : make_float4(3.0f * v[0][0], 3.0f * v[0][1], 3.0f * v[0][2], 0.0f);
+    ref_array<Q>(buf, g.pop, 0)[((long long)(z * g.ny + y) * g.px + x0) >> 1] = J;
 }
 
 // Read the state back as dense FP64 [Q][N].
@@ -741,7 +955,19 @@ cudaError_t launch_step(const void *fin, void *fout, const StepArgs &a, cudaStre
         io.in[q] = static_cast<const T *>(fin) + (q < Q ? q * a.g.pop : 0);
         io.out[q] = static_cast<T *>(fout) + (q < Q ? q * a.g.pop : 0);
     }
+    io.ref_in = Storage<T>::kRef ? ref_array<Q>(static_cast<const T *>(fin), a.g.pop, 0) : nullptr;
+    io.ref_out = Storage<T>::kRef ? ref_array<Q>(static_cast<T *>(fout), a.g.pop, 0) : nullptr;
     const bool walls = a.g.bc != 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (a.sr32) {  // stochastically rounded FP32 update: the one-cell kernel, any nx
+            const CellLaunch L = cell_launch(a.g);
+            if (walls)
+                step_kernel<Q, T, true, true><<<L.grid, L.block, 0, st>>>(io, a);
+            else
+                step_kernel<Q, T, false, true><<<L.grid, L.block, 0, st>>>(io, a);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (Q == 27) {
         if (a.g.nx % 2 == 0) {
             Grid half = a.g;
@@ -786,12 +1012,19 @@ cudaError_t launch_step_aa(void *buf, const StepArgs &a, bool even, cudaStream_t
         io.in[q] = static_cast<const T *>(buf) + (q < Q ? q * a.g.pop : 0);
         io.out[q] = static_cast<T *>(buf) + (q < Q ? q * a.g.pop : 0);
     }
+    // BF16 references: array 0 for the natural layout, 1 for the swapped one
+    io.ref_in = Storage<T>::kRef ? ref_array<Q>(static_cast<const T *>(buf), a.g.pop, even ? 0 : 1)
+                                 : nullptr;
+    io.ref_out = Storage<T>::kRef ? ref_array<Q>(static_cast<T *>(buf), a.g.pop, even ? 1 : 0)
+                                  : nullptr;
     Grid half = a.g;
     half.nx = a.g.nx / 2;
     const CellLaunch L = cell_launch(half);
     const PackedRates pr = packed_rates(a, kFoldedLoad<Q, T>());
-    if (even)
-        aa_even_kernel<Q, T><<<L.grid, L.block, 0, st>>>(io, a, pr);
+    if (even && a.g.bc)
+        aa_even_kernel<Q, T, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+    else if (even)
+        aa_even_kernel<Q, T, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
     else if (a.g.bc)
         aa_odd_kernel<Q, T, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
     else
@@ -799,9 +1032,24 @@ cudaError_t launch_step_aa(void *buf, const StepArgs &a, bool even, cudaStream_t
     return cudaGetLastError();
 }
 
+// BF16: the references of the state being loaded, before its values.
+template <int Q, typename T>
+cudaError_t launch_ref_init(T *buf, const Grid &g, const double *u, const double *f,
+                            cudaStream_t st) {
+    Grid half = g;
+    half.nx = (g.nx + 1) / 2;
+    const CellLaunch L = cell_launch(half);
+    ref_init_kernel<Q, T><<<L.grid, L.block, 0, st>>>(buf, g, u, f);
+    return cudaGetLastError();
+}
+
 template <int Q, typename T>
 cudaError_t launch_init(void *buf, const StepArgs &a, const double *rho, const double *u,
                         cudaStream_t st) {
+    if constexpr (Storage<T>::kRef) {
+        const cudaError_t e = launch_ref_init<Q, T>(static_cast<T *>(buf), a.g, u, nullptr, st);
+        if (e != cudaSuccess) return e;
+    }
     const CellLaunch L = cell_launch(a.g);
     init_kernel<Q, T><<<L.grid, L.block, 0, st>>>(static_cast<T *>(buf), a, rho, u);
     return cudaGetLastError();
@@ -809,6 +1057,10 @@ cudaError_t launch_init(void *buf, const StepArgs &a, const double *rho, const d
 
 template <int Q, typename T>
 cudaError_t launch_set_state(void *buf, const Grid &g, const double *f, cudaStream_t st) {
+    if constexpr (Storage<T>::kRef) {
+        const cudaError_t e = launch_ref_init<Q, T>(static_cast<T *>(buf), g, nullptr, f, st);
+        if (e != cudaSuccess) return e;
+    }
     const CellLaunch L = cell_launch(g);
     set_state_kernel<Q, T><<<L.grid, L.block, 0, st>>>(static_cast<T *>(buf), g, f);
     return cudaGetLastError();

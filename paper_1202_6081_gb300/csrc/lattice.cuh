@@ -103,6 +103,7 @@ struct Storage;
 template <>
 struct Storage<float> {
     static constexpr bool kScaled = false;
+    static constexpr bool kRef = false;
     __device__ __forceinline__ static float load(const float *p) { return __ldg(p); }
     __device__ __forceinline__ static void store(float *p, float v) { __stcs(p, v); }
 };
@@ -110,6 +111,7 @@ struct Storage<float> {
 template <>
 struct Storage<__half> {
     static constexpr bool kScaled = true;
+    static constexpr bool kRef = false;
     __device__ __forceinline__ static float load(const __half *p) {
         return __half2float(__ldg(p));
     }
@@ -121,6 +123,7 @@ struct Storage<__half> {
 template <>
 struct Storage<__nv_bfloat16> {
     static constexpr bool kScaled = true;
+    static constexpr bool kRef = true;  // momentum references, see below
     __device__ __forceinline__ static float load(const __nv_bfloat16 *p) {
         return __bfloat162float(__ldg(p));
     }
@@ -171,6 +174,23 @@ __device__ __forceinline__ unsigned sr_bits(unsigned seed) {
     return seed ^ (0x9E3779B9u * static_cast<unsigned>(q + 1));
 }
 
+// a + b rounded stochastically to FP32.  The exact sum lies between
+// s = fl(a + b) and the neighbour n of s toward the residual r = (a + b) - s,
+// which an error-free transformation (Knuth's two-sum, six operations, no
+// contraction) gives exactly; n is taken with probability |r| / |n - s|,
+// from the top 24 of the 32 random bits.  Used by the opt-in stochastically
+// rounded FP32 update (LBM_F32_SR).
+__device__ __forceinline__ float add_sr32(float a, float b, unsigned bits) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float r = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    if (r == 0.0f) return s;
+    const float n = nextafterf(s, r > 0.0f ? INFINITY : -INFINITY);
+    const float gap = fabsf(__fsub_rn(n, s));  // a power of two: exact
+    const float u = __uint2float_rz(bits >> 8) * 0x1p-24f;
+    return __fmul_rn(u, gap) < fabsf(r) ? n : s;
+}
+
 // (lo, hi) -> packed 16-bit pair (lo in the low half), stochastically rounded.
 template <typename T>
 struct PackSR;
@@ -195,21 +215,23 @@ __device__ __forceinline__ unsigned pack_sr(float lo, float hi, unsigned seed) {
     return PackSR<T>::run(lo, hi, sr_bits<q>(seed));
 }
 
-// Deviation f - w (FP32) -> stored value.
+// Deviation f - w (FP32) -> stored value (ref: the value's momentum
+// reference, 0 unless the storage keeps one).
 template <int Q, typename T>
-__device__ __forceinline__ void store_dev(T *p, int a, float dev) {
+__device__ __forceinline__ void store_dev(T *p, int a, float dev, float ref = 0.0f) {
     if (Storage<T>::kScaled)
-        Storage<T>::store(p, dev * float(1.0 / weight<Q>(a)));
+        Storage<T>::store(p, dev * float(1.0 / weight<Q>(a)) - ref);
     else
         Storage<T>::store(p, dev);
 }
 
 // The step's store of population a of one cell: FP32 as is, 16-bit
-// stochastically rounded.
+// stochastically rounded (ref: as for store_dev).
 template <int Q, typename T, int a>
-__device__ __forceinline__ void store_dev_step(T *p, float dev, unsigned seed) {
+__device__ __forceinline__ void store_dev_step(T *p, float dev, unsigned seed, float ref = 0.0f) {
     if constexpr (Storage<T>::kScaled) {
-        const unsigned d = pack_sr<T, a>(dev * float(1.0 / weight<Q>(a)), 0.0f, seed);
+        const unsigned d =
+            pack_sr<T, a>(fmaf(dev, float(1.0 / weight<Q>(a)), -ref), 0.0f, seed);
         __stcs(reinterpret_cast<unsigned short *>(p), static_cast<unsigned short>(d & 0xffffu));
     } else {
         Storage<T>::store(p, dev);
@@ -238,6 +260,63 @@ struct Grid {
     long long pop;    // px * ny * nz: distance between populations
     int layout;       // kPull, kAANatural or kAASwapped (state reads and writes)
 };
+
+// ------------------------------------------------- BF16 momentum references
+// BF16 keeps 8 significant bits, and (f - w)/w is O(3 |u|) in a moving flow:
+// its rounding noise alone puts the velocity 1.4e-3 (relative L2) off.  So a
+// BF16 state buffer stores, for every population a with one or two nonzero
+// velocity components (the axis and edge populations, which carry ~95 % of
+// the momentum's weight), the value relative to the linear part of the local
+// equilibrium,
+//     stored_a = (f_a - w_a) / w_a - e_a . J,
+// where J = 3 u-bar is three times the mean velocity of the pair of cells
+// (x even, x + 1) that produced the value (the cell whose collision wrote
+// it).  The rest is O(u^2) plus the non-equilibrium part, an order of
+// magnitude smaller, and so is its rounding.  The corners (|e|^2 = 3) keep
+// (f - w)/w.  J of every pair sits in an FP32 array after the population
+// planes of the buffer, float4 (Jx, Jy, Jz, 0) per pair of the pitched row,
+// 8 bytes per cell; the in-place scheme keeps two such arrays (index 0 for
+// the natural layout, 1 for the swapped one).
+//
+// Who produced a value: the pre-collision f_a(x) is population a of the
+// cell x - e_a after its collision, or, behind a bounce-back wall,
+// population opp(a) of x itself, whatever the layout.  So a reader adds
+// e_a . J(pair of x - e_a), or -e_a . J(pair of x) behind a wall.
+template <int Q>
+__host__ __device__ constexpr bool has_ref(int a) {
+    return ex<Q>(a) * ex<Q>(a) + ey<Q>(a) * ey<Q>(a) + ez<Q>(a) * ez<Q>(a) <= 2 &&
+           (ex<Q>(a) != 0 || ey<Q>(a) != 0 || ez<Q>(a) != 0);
+}
+
+// e_a . J with the components of population a known at compile time.
+template <int Q, int a>
+__device__ __forceinline__ float ref_dot(const float4 &J) {
+    constexpr int cx = ex<Q>(a), cy = ey<Q>(a), cz = ez<Q>(a);
+    float r = 0.0f;
+    bool first = true;
+    if constexpr (cx != 0) {
+        r = cx > 0 ? J.x : -J.x;
+        first = false;
+    }
+    if constexpr (cy != 0) {
+        r = first ? (cy > 0 ? J.y : -J.y) : (cy > 0 ? r + J.y : r - J.y);
+        first = false;
+    }
+    if constexpr (cz != 0) r = first ? (cz > 0 ? J.z : -J.z) : (cz > 0 ? r + J.z : r - J.z);
+    return r;
+}
+
+// Reference array `which` of a state buffer of storage T (pop = elements per
+// population plane, even).  Pair of the element at offset e: e >> 1 (rows
+// start at even offsets).
+template <int Q, typename T>
+__host__ __device__ inline const float4 *ref_array(const T *buf, long long pop, int which) {
+    return reinterpret_cast<const float4 *>(buf + (long long)Q * pop) + (long long)which * (pop / 2);
+}
+template <int Q, typename T>
+__host__ __device__ inline float4 *ref_array(T *buf, long long pop, int which) {
+    return reinterpret_cast<float4 *>(buf + (long long)Q * pop) + (long long)which * (pop / 2);
+}
 
 // Source coordinates of the pull for one cell.  Index 0, 1, 2 of each array
 // is the velocity component -1, 0, +1; the source along an axis is the cell
@@ -296,7 +375,17 @@ __device__ __forceinline__ void gather(const T *__restrict__ fin, const Grid &g,
         } else {
             idx = (long long)(g.layout == kPull ? a : o) * g.pop + s.row[j][k] + s.xs[i];
         }
-        const float v = Storage<T>::load(fin + idx);
+        float v = Storage<T>::load(fin + idx);
+        if constexpr (Storage<T>::kRef) {
+            if (has_ref<Q>(a)) {
+                // producer: x - e_a, or x itself behind a wall (population opp(a))
+                const float4 *R = ref_array<Q>(fin, g.pop, g.layout == kAASwapped ? 1 : 0);
+                const long long prod = s.wall[j][k] ? s.own : s.row[j][k] + s.xs[i];
+                const float4 J = __ldg(R + (prod >> 1));
+                const float r = ex<Q>(a) * J.x + ey<Q>(a) * J.y + ez<Q>(a) * J.z;
+                v += s.wall[j][k] ? -r : r;
+            }
+        }
         // the weight of a slot and of its opposite are equal
         f[a] = Storage<T>::kScaled ? v * float(weight<Q>(a)) : v;
     }
@@ -305,22 +394,32 @@ __device__ __forceinline__ void gather(const T *__restrict__ fin, const Grid &g,
 // Inverse of the pull: place the pre-collision values f_alpha(x) of one cell
 // where the next step will read them (used to load a state; the AA scheme
 // loads into its natural layout).
+// With momentum references (BF16) the reference array 0 must already hold J
+// of every pair (ref_init_kernel), and each value is stored relative to the
+// reference of its producer, as a reader will add it back.
 template <int Q, typename T>
 __device__ __forceinline__ void scatter_state(T *__restrict__ buf, const Grid &g,
                                               const PullSources &s, const float (&f)[Q]) {
-    if (g.layout != kPull) {
-#pragma unroll
-        for (int a = 0; a < Q; ++a) store_dev<Q, T>(buf + (long long)a * g.pop + s.own, a, f[a]);
-        return;
-    }
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int j = ey<Q>(a) + 1, k = ez<Q>(a) + 1, i = ex<Q>(a) + 1;
-        if (s.wall[j][k]) {
+        float ref = 0.0f;
+        if constexpr (Storage<T>::kRef) {
+            if (has_ref<Q>(a)) {
+                const float4 *R = ref_array<Q>(static_cast<const T *>(buf), g.pop, 0);
+                const long long prod = s.wall[j][k] ? s.own : s.row[j][k] + s.xs[i];
+                const float4 J = R[prod >> 1];
+                const float r = ex<Q>(a) * J.x + ey<Q>(a) * J.y + ez<Q>(a) * J.z;
+                ref = s.wall[j][k] ? -r : r;
+            }
+        }
+        if (g.layout != kPull) {
+            store_dev<Q, T>(buf + (long long)a * g.pop + s.own, a, f[a], ref);
+        } else if (s.wall[j][k]) {
             const int o = opposite<Q>(a);
-            store_dev<Q, T>(buf + (long long)o * g.pop + s.own, o, f[a]);
+            store_dev<Q, T>(buf + (long long)o * g.pop + s.own, o, f[a], ref);
         } else {
-            store_dev<Q, T>(buf + (long long)a * g.pop + s.row[j][k] + s.xs[i], a, f[a]);
+            store_dev<Q, T>(buf + (long long)a * g.pop + s.row[j][k] + s.xs[i], a, f[a], ref);
         }
     }
 }

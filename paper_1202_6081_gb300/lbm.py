@@ -28,6 +28,7 @@ LBM_STORE_BF16 = 2
 LBM_WALL_Y = 1
 LBM_WALL_Z = 2
 LBM_INPLACE = 4
+LBM_F32_SR = 8
 STORAGE = {"f32": LBM_STORE_F32, "f16": LBM_STORE_F16, "bf16": LBM_STORE_BF16}
 
 LBM_OK = 0
@@ -267,10 +268,11 @@ class Solver:
     uniform F (3,) or a per-cell field [3, nz, ny, nx] (device FP32 tensor or
     array); walls: OR of LBM_WALL_Y / LBM_WALL_Z; storage: "f32", "f16" or
     "bf16"; inplace: one state buffer with in-place (AA) streaming (nx
-    even; no step_into / adjoint)."""
+    even; no step_into / adjoint); sr32: stochastically rounded FP32 update
+    (LBM_F32_SR; FP32 storage, not in place)."""
 
     def __init__(self, Q, shape, omega, force=(0.0, 0.0, 0.0), walls=0, storage="f32",
-                 device=None, inplace=False):
+                 device=None, inplace=False, sr32=False):
         self.Q = int(Q)
         self.shape = tuple(int(s) for s in shape)
         nz, ny, nx = self.shape
@@ -290,7 +292,7 @@ class Solver:
                 field = torch.as_tensor(F, dtype=torch.float32).reshape(3, nz, ny, nx)
                 field = field.to(self.device).contiguous()
             self.force_field = field
-            flags = walls | (LBM_INPLACE if self.inplace else 0)
+            flags = walls | (LBM_INPLACE if self.inplace else 0) | (LBM_F32_SR if sr32 else 0)
             self.ctx = lbm_create(self.Q, nx, ny, nz, self.omega, uniform, flags, STORAGE[storage])
             nbytes = lbm_state_bytes(self.ctx)
             self.buffers = [torch.empty(nbytes, dtype=torch.uint8, device=self.device)

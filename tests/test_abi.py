@@ -46,12 +46,14 @@ def _om(Q, v=1.5):
 
 
 @pytest.mark.parametrize("args", [
-    dict(lattice=19), dict(nx=0), dict(ny=-1), dict(nz=0), dict(bc=8), dict(storage=3),
+    dict(lattice=19), dict(nx=0), dict(ny=-1), dict(nz=0), dict(bc=16), dict(storage=3),
     dict(bc=4, nx=5), dict(bc=7, nx=7),  # in-place streaming takes cell pairs: nx even
     dict(nx=2048, ny=1024, nz=1024),      # 2^31 cells: beyond 32-bit plane offsets
     dict(nx=1, ny=65536, nz=1),           # launch grid limit in y
     dict(omega_value=2.0), dict(omega_value=0.0), dict(omega_value=float("nan")),
     dict(force=(float("inf"), 0.0, 0.0)), dict(omega_null=True), dict(out_null=True),
+    dict(bc=8, storage=1), dict(bc=8, storage=2),  # stochastic FP32 update: FP32 storage only
+    dict(bc=12, nx=6),                             # and not in place
 ])
 def test_create_rejects_bad_arguments_before_touching_cuda(lib, args):
     Q = args.get("lattice", 27)

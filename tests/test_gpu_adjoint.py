@@ -96,7 +96,7 @@ def test_gradient_matches_fp64_finite_differences(lbm, orc):
     """16^3 periodic, Taylor-Green + noise, Gaussian force field (RMS 1e-5),
     200 steps, checkpoint every 20: the GPU adjoint gradient matches FP64
     central differences of the oracle (eps = 1e-6) on 16 sampled
-    (cell, component) pairs to 1e-3."""
+    (cell, component) pairs, each within 1e-3 of its own value."""
     from paper_1202_6081_gb300.autograd import kinetic_energy_after
     Q = 27
     shape = (16, 16, 16)
@@ -125,14 +125,75 @@ def test_gradient_matches_fp64_finite_differences(lbm, orc):
     fd = np.array(fd)
     got = np.array([g[k, z, y, x] for (c, (z, y, x)), k in zip(samples, comps)])
     print("fd", fd[:4], "adjoint", got[:4])
-    assert np.abs(got - fd).max() <= 1e-3 * np.abs(fd).max()
+    assert_per_element(got, fd)
+
+
+def assert_per_element(got, fd, rel=1e-3, floor=1e-5):
+    """Every sampled derivative on its own: |got - fd| <= rel |fd| plus a
+    small floor relative to the largest sampled derivative (for entries
+    near zero)."""
+    err = np.abs(got - fd)
+    bound = rel * np.abs(fd) + floor * np.abs(fd).max()
+    print("per-element |adjoint - fd| / |fd|:", np.array2string(err / np.abs(fd), precision=2))
+    assert np.all(err <= bound), (got, fd)
+
+
+def test_gradient_32cubed_matches_fp64_oracle_differences(lbm, orc):
+    """The adjoint workload's recipe at 32^3: D3Q27 periodic, tau = 0.6,
+    Taylor-Green + noise, Gaussian force field (RMS 1e-5, sigma 4), J after
+    200 steps, checkpoint every 20.  The GPU gradient against FP64 central
+    differences of the oracle on 16 (cell, component) pairs, each within
+    1e-3 of its own value (plus a 1e-5 floor of the largest).  The step
+    eps = 1e-8 (1e-3 of the force's RMS) lies on a plateau: on four of the
+    pairs the difference quotient at eps = 1e-7 agrees to 1e-4 (measured
+    ~1e-7; at 1e-9 FP64 roundoff starts to show, ~4e-7)."""
+    from paper_1202_6081_gb300.autograd import kinetic_energy_after
+    Q = 27
+    shape = (32, 32, 32)
+    om = W.omegas(Q, 1 / 0.6)
+    rho, u = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    F0 = f32(W.gaussian_force_field(shape, rms=1e-5, sigma=4.0))
+    S = lbm.Solver(Q, shape, om)
+    Ft = torch.as_tensor(F0, dtype=torch.float32, device="cuda").contiguous().requires_grad_()
+    S.set_force_field(Ft.detach())
+    S.init_equilibrium(rho, u)
+    f0 = orc.equilibrium(Q, rho, u, F0)
+    J = kinetic_energy_after(S, Ft, 200, 20)
+    J.backward()
+    g = Ft.grad.cpu().numpy()
+    cells = W.sample_cells(shape, 16, seed=43)
+    comps = W.rng(44).integers(0, 3, size=len(cells))
+
+    def quotient(z, y, x, k, eps):
+        Fp, Fm = F0.copy(), F0.copy()
+        Fp[k, z, y, x] += eps
+        Fm[k, z, y, x] -= eps
+        jp = orc.kinetic_energy(Q, orc.run(Q, shape, f0, Fp, om, 200), Fp)
+        jm = orc.kinetic_energy(Q, orc.run(Q, shape, f0, Fm, om, 200), Fm)
+        return (jp - jm) / (2 * eps)
+
+    fd, got = [], []
+    for n, (c, k) in enumerate(zip(cells, comps)):
+        z, y, x = (int(v) for v in np.unravel_index(c, shape))
+        q8 = quotient(z, y, x, k, 1e-8)
+        if n < 4:
+            q7 = quotient(z, y, x, k, 1e-7)
+            assert abs(q7 - q8) <= 1e-4 * abs(q8), (q7, q8)
+        fd.append(q8)
+        got.append(g[k, z, y, x])
+    fd, got = np.array(fd), np.array(got)
+    print("fd", fd[:4], "adjoint", got[:4])
+    assert_per_element(got, fd)
 
 
 def test_gradient_128cubed_matches_gpu_finite_differences(lbm):
-    """The adjoint workload: D3Q27, 128^3 periodic, tau = 0.6, Taylor-Green +
-    noise, Gaussian force field RMS 1e-5, J after 200 steps, checkpoint every
-    20: the gradient matches central differences of the GPU forward on 16
-    random cells to 1e-3 (relative to the largest sampled gradient)."""
+    """The adjoint workload itself: D3Q27, 128^3 periodic, tau = 0.6,
+    Taylor-Green + noise, Gaussian force field RMS 1e-5, J after 200 steps,
+    checkpoint every 20.  A check that the workload runs end to end: the
+    gradient matches central differences of the GPU's own FP32 forward on 16
+    random cells to 1e-3 relative to the largest sampled gradient (those
+    differences carry FP32 noise of about that size; the check against the
+    FP64 definition is the 32^3 test above)."""
     from paper_1202_6081_gb300.autograd import kinetic_energy_after
     Q = 27
     shape = (128, 128, 128)
@@ -249,8 +310,8 @@ def test_macroscopic_after_gradients_match_fp64_differences(lbm, orc, Q):
         gotf.append(gf0[a, z, y, x])
     fdF, gotF, fdf, gotf = map(np.array, (fdF, gotF, fdf, gotf))
     print("dJ/dF fd", fdF[:3], "adjoint", gotF[:3], "; dJ/df0 fd", fdf[:3], "adjoint", gotf[:3])
-    assert np.abs(gotF - fdF).max() <= 1e-3 * np.abs(fdF).max()
-    assert np.abs(gotf - fdf).max() <= 1e-3 * np.abs(fdf).max()
+    assert_per_element(gotF, fdF)
+    assert_per_element(gotf, fdf)
 
 
 @pytest.mark.parametrize("Q", [27, 15])

@@ -36,14 +36,16 @@ def orc():
     return oracle
 
 
-def plates_steady(lbm, Q, N, omega_nu, Fx):
+def plates_steady(lbm, Q, N, omega_nu, Fx, sr32=False):
     """Steady force-driven flow between plates: 3 x 3 x (N - 2) fluid cells,
-    walls on the z faces; returns (z, u_x(z), u_analytic(z), nu, L)."""
+    walls on the z faces; returns (z, u_x(z), u_analytic(z), nu, L).
+    sr32: the stochastically rounded FP32 update (LBM_F32_SR)."""
     nz = N - 2
     shape = (nz, 3, 3)
     L = nz / 2
     nu = analytic.viscosity(omega_nu)
-    S = lbm.Solver(Q, shape, W.omegas(Q, omega_nu), force=(Fx, 0.0, 0.0), walls=lbm.LBM_WALL_Z)
+    S = lbm.Solver(Q, shape, W.omegas(Q, omega_nu), force=(Fx, 0.0, 0.0), walls=lbm.LBM_WALL_Z,
+                   sr32=sr32)
     S.init_equilibrium(np.ones(shape), np.zeros((3,) + shape))
     # the slowest mode decays as exp(-nu (pi / 2L)^2 t): run to e^-16
     steps = int(16 * 4 * L * L / (nu * np.pi**2)) + 1
@@ -92,26 +94,39 @@ def _oracle_plates_error(orc, Q, N, omega_nu, Fx):
 
 def test_grid_convergence_matches_fp64(lbm, orc):
     """Sec. 9 convergence study (D3Q15, 3 x 3 x N, omega 1.818, F_x = 6.958e-6
-    at N = 13 scaled as 1/L^3, diffusive scaling).  At N = 13 and 25 the
-    FP32 GPU errors equal the FP64 oracle's (second order: the oracle's slope
-    against L is -2.0, pinned in test_oracle_pins).  Finer grids meet the
-    FP32 storage floor: the scaled force per step (9e-8 at N = 49, 1e-8 at
-    N = 97) is a few hundred ulps of the stored deviations and the same
-    rounding repeats every step at steady state, so the error stops falling
-    near 3e-4; those are printed, not held."""
+    at N = 13 scaled as 1/L^3, diffusive scaling), N = 13, 25, 49, 97.  With
+    the stochastically rounded FP32 update (LBM_F32_SR) the GPU errors equal
+    the FP64 oracle's at N = 13, 25 and fall with a log-log slope in
+    [-2.1, -1.9] against L (the paper reports -1.96; the oracle's -2.0 is
+    pinned in test_oracle_pins).  The default round-to-nearest update is
+    printed beside it: at steady state it makes the same rounding error at
+    every step, and on the finest grids (where the scaled force per step is
+    1e-8) those errors, accumulated in the slowest mode, leave it off the
+    second-order line; it is held only to 1e-3."""
     L13 = (13 - 2) / 2
+    Ls, errs = [], []
     for N in (13, 25, 49, 97):
         L = (N - 2) / 2
         Fx = 6.958e-6 * (L13 / L) ** 3
-        z, ux, ua, nu, _ = plates_steady(lbm, 15, N, 1.818, Fx)
+        _, ux, ua, _, _ = plates_steady(lbm, 15, N, 1.818, Fx, sr32=True)
         err = np.linalg.norm(ux - ua) / np.linalg.norm(ua)
+        _, ux_rn, _, _, _ = plates_steady(lbm, 15, N, 1.818, Fx)
+        err_rn = np.linalg.norm(ux_rn - ua) / np.linalg.norm(ua)
+        line = "N %d: F %.3e, rel L2 error %.4e (round-to-nearest update %.4e)" % (N, Fx, err,
+                                                                                 err_rn)
         if N <= 25:
             want = _oracle_plates_error(orc, 15, N, 1.818, Fx)
-            print("N %d: F %.3e, rel L2 error %.4e (FP64 oracle %.4e)" % (N, Fx, err, want))
+            print(line + ", FP64 oracle %.4e" % want)
             assert err == pytest.approx(want, rel=1e-2)
+            assert err_rn == pytest.approx(want, rel=1e-2)
         else:
-            print("N %d: F %.3e, rel L2 error %.4e" % (N, Fx, err))
-            assert err <= 1e-3
+            print(line)
+            assert err_rn <= 1e-3
+        Ls.append(L)
+        errs.append(err)
+    slope = np.polyfit(np.log(Ls), np.log(errs), 1)[0]
+    print("log-log slope of the error against L: %.3f" % slope)
+    assert -2.1 <= slope <= -1.9
 
 
 def _womersley_run(lbm, Q, omega_nu, steps, T=10000, Fm=1e-5, sample_every=None, u0=None):
