@@ -251,6 +251,15 @@ template <int Q>
 __device__ __forceinline__ unsigned pair_seed(const f2 (&f)[Q], int own) {
     return sr_seed(f[1].v ^ f[6].v ^ f[kSeedPop<Q>].v ^ f[Q - 1].v, own);
 }
+// Which values the pair kernels hash: the pre-collision ones, or for D3Q15
+// with FP16 storage the post-collision ones (either is a fixed function of
+// the state; chosen by measurement: D3Q15 FP16 68.0k vs 62.4k MLUPS at 256^3
+// hashing after the collision, D3Q15 BF16 61.5k vs 64.0k and D3Q27 the same
+// or better before it).  The in-place kernels make the same choice, so that
+// their states stay bit-identical to the two-buffer step's.
+template <int Q, typename T>
+constexpr bool kSeedAfterCollision = Q == 15 && Storage<T>::kScaled && !Storage<T>::kRef;
+
 template <int Q>
 __device__ __forceinline__ unsigned cell_seed(const float (&f)[Q], int own) {
     const unsigned a = __float_as_uint(f[1]) ^ __float_as_uint(f[6]);
@@ -330,7 +339,28 @@ __device__ __forceinline__ Rows<kWalls> pull_rows(const Grid &g, int y, int z) {
 // Reader: adds to the pulled raw values f[q] of cells (x0, x0 + 1) the
 // reference of each value's producer: for e_x = 0 both from the pair of the
 // source row, for e_x = +1 from the pairs of x0 - 1 and x0, for e_x = -1 of
-// x0 + 1 and x0 + 2; behind a wall minus that of the own pair.
+// x0 + 1 and x0 + 2; behind a wall minus that of the own pair.  A source row
+// (e_y, e_z) needs two components of J at most, loaded narrow to keep
+// registers free: the row e_y = e_z = 0 only Jx (axis populations), rows
+// with e_z = 0 (Jx, Jy), rows with e_y = 0 (Jz, Jx) -- J is stored as
+// (Jx, Jy, Jz, Jx) so that both pairs are aligned 8-byte loads -- and the
+// rows with e_y, e_z both nonzero (Jy, Jz), only of the own column (their
+// corners carry no reference).
+template <int ey, int ez>
+__device__ __forceinline__ float4 load_ref(const float4 *p) {
+    if constexpr (ey == 0 && ez == 0) {
+        return make_float4(__ldg(&p->x), 0.0f, 0.0f, 0.0f);
+    } else if constexpr (ez == 0) {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        return make_float4(v.x, v.y, 0.0f, 0.0f);
+    } else if constexpr (ey == 0) {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p) + 1);
+        return make_float4(v.y, 0.0f, v.x, 0.0f);
+    } else {
+        return __ldg(p);
+    }
+}
+
 template <int Q, bool kWalls>
 __device__ __forceinline__ void add_refs_pair(const float4 *__restrict__ ref, const Rows<kWalls> &R,
                                               int x0, int xm, int xp, f2 (&f)[Q]) {
@@ -338,20 +368,21 @@ __device__ __forceinline__ void add_refs_pair(const float4 *__restrict__ ref, co
         constexpr int q = decltype(iq)::value;
         if constexpr (has_ref<Q>(q)) {
             constexpr int i = ex<Q>(q), j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
+            constexpr int cy = ey<Q>(q), cz = ez<Q>(q);
             float rlo, rhi;
             if (kWalls && R.wall[j][k]) {
-                rlo = rhi = -ref_dot<Q, q>(__ldg(ref + ((R.own + x0) >> 1)));
+                rlo = rhi = -ref_dot<Q, q>(load_ref<cy, cz>(ref + ((R.own + x0) >> 1)));
             } else {
                 const float4 *row = ref + (R.off[j][k] >> 1);
-                const float4 C = __ldg(row + (x0 >> 1));
+                const float4 C = load_ref<cy, cz>(row + (x0 >> 1));
                 if constexpr (i == 0) {
                     rlo = rhi = ref_dot<Q, q>(C);
                 } else if constexpr (i == 1) {
-                    rlo = ref_dot<Q, q>(__ldg(row + (xm >> 1)));
+                    rlo = ref_dot<Q, q>(load_ref<cy, cz>(row + (xm >> 1)));
                     rhi = ref_dot<Q, q>(C);
                 } else {
                     rlo = ref_dot<Q, q>(C);
-                    rhi = ref_dot<Q, q>(__ldg(row + (xp >> 1)));
+                    rhi = ref_dot<Q, q>(load_ref<cy, cz>(row + (xp >> 1)));
                 }
             }
             f[q] = f[q] + f2(rlo, rhi);
@@ -361,8 +392,8 @@ __device__ __forceinline__ void add_refs_pair(const float4 *__restrict__ ref, co
 
 // Writer: the pair's reference J = 3 u-bar (mean velocity of the two cells).
 __device__ __forceinline__ float4 pair_ref(f2 ux, f2 uy, f2 uz) {
-    return make_float4(1.5f * (ux.lo() + ux.hi()), 1.5f * (uy.lo() + uy.hi()),
-                       1.5f * (uz.lo() + uz.hi()), 0.0f);
+    const float jx = 1.5f * (ux.lo() + ux.hi());
+    return make_float4(jx, 1.5f * (uy.lo() + uy.hi()), 1.5f * (uz.lo() + uz.hi()), jx);
 }
 
 // Stored value of population q of a pair from its post-collision value v
@@ -436,6 +467,7 @@ __global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const Ste
             J = make_float4(1.5f * (ux + px), 1.5f * (uy + py), 1.5f * (uz + pz), 0.0f);
         else
             J = make_float4(3.0f * ux, 3.0f * uy, 3.0f * uz, 0.0f);
+        J.w = J.x;
         if (!inside) return;
         if ((x & 1) == 0) __stcs(io.ref_out + ((R.own + x) >> 1), J);
     }
@@ -453,11 +485,11 @@ __global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const Ste
 // e_x = +-1 sources are two single loads (x0 - 1, x0) or (x0 + 1, x0 + 2).
 // Blocks of 128 per SM, by measurement: FP32 storage 5 (96 registers, no
 // spills; 6 blocks ran the same, 32.20k vs 32.23k MLUPS at 256^3, and 7
-// slower); 16-bit storage 6 (80 registers, ~260 bytes of spills): FP16
-// 38.0k / 40.1k / 42.3k / 38.5k / 25.1k MLUPS at 4 / 5 / 6 / 7 / 8 blocks at
-// 512^3, BF16 39.2k at 5 and 42.2k at 6.
+// slower); FP16 storage 6 (80 registers, 64 bytes of spills): 41.2k / 44.3k
+// / 37.5k MLUPS at 5 / 6 / 7 blocks at 512^3; BF16 (with its reference
+// loads) 5: 38.1k / 37.0k / 32.0k.
 template <typename T>
-constexpr int kStep2Blocks = Storage<T>::kScaled ? 6 : 5;
+constexpr int kStep2Blocks = Storage<T>::kRef ? 5 : Storage<T>::kScaled ? 6 : 5;
 
 template <typename T, bool kWalls>
 __global__ void __launch_bounds__(128, kStep2Blocks<T>) step2_kernel(const StepIO<T> io,
@@ -559,7 +591,8 @@ __global__ void __launch_bounds__(128, kQ15Blocks<T>) step2_q15_kernel(const Ste
             f[q] = f[q] * f2(float(weight<15>(q)));
         });
     }
-    const unsigned seed = pair_seed<15>(f, R.own + x0);
+    unsigned seed = 0;
+    if constexpr (!kSeedAfterCollision<15, T>) seed = pair_seed<15>(f, R.own + x0);
     f2 Fx, Fy, Fz;
     if (a.Ffield) {
         const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
@@ -582,6 +615,7 @@ __global__ void __launch_bounds__(128, kQ15Blocks<T>) step2_q15_kernel(const Ste
         J = pair_ref(ux, uy, uz);
         __stcs(io.ref_out + ((R.own + x0) >> 1), J);
     }
+    if constexpr (kSeedAfterCollision<15, T>) seed = pair_seed<15>(f, R.own + x0);
     static_for<15>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
         const f2 v = stored_pair<15, T, q>(f[q], store_scale<15, T>(q), J);
@@ -688,8 +722,10 @@ __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const 
         f[q] = Pair<T>::ld2(io.in[q] + own);
     });
     pair_inputs<Q, T, kWalls>(io, R, x0, xm, xp, f);
-    const unsigned seed = pair_seed<Q>(f, own);
+    unsigned seed = 0;
+    if constexpr (!kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
     const float4 J = pair_collide<Q, T>(io, a, pr, x0, y, z, own, f);
+    if constexpr (kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
         const f2 v = stored_pair<Q, T, q>(f[q], store_scale<Q, T>(q), J);
@@ -734,8 +770,10 @@ __global__ void __launch_bounds__(128, (kAAOddBlocks<Q, T>))
         f[q] = v;
     });
     pair_inputs<Q, T, kWalls>(io, R, x0, xm, xp, f);
-    const unsigned seed = pair_seed<Q>(f, own);
+    unsigned seed = 0;
+    if constexpr (!kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
     const float4 J = pair_collide<Q, T>(io, a, pr, x0, y, z, own, f);
+    if constexpr (kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
         constexpr int i = ex<Q>(q), j = ey<Q>(q) + 1, k = ez<Q>(q) + 1;
@@ -819,9 +857,10 @@ __global__ void __launch_bounds__(128) ref_init_kernel(T *__restrict__ buf, cons
             }
             v[m][d] = float(sum);
         }
-    const float4 J = n == 2 ? make_float4(1.5f * (v[0][0] + v[1][0]), 1.5f * (v[0][1] + v[1][1]),
-                                          1.5f * (v[0][2] + v[1][2]), 0.0f)
-                            : make_float4(3.0f * v[0][0], 3.0f * v[0][1], 3.0f * v[0][2], 0.0f);
+    float4 J = n == 2 ? make_float4(1.5f * (v[0][0] + v[1][0]), 1.5f * (v[0][1] + v[1][1]),
+                                    1.5f * (v[0][2] + v[1][2]), 0.0f)
+                      : make_float4(3.0f * v[0][0], 3.0f * v[0][1], 3.0f * v[0][2], 0.0f);
+    J.w = J.x;  // stored as (Jx, Jy, Jz, Jx): see load_ref
     ref_array<Q>(buf, g.pop, 0)[((long long)(z * g.ny + y) * g.px + x0) >> 1] = J;
 }
 

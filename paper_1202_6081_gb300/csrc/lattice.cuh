@@ -144,7 +144,8 @@ struct Storage<__nv_bfloat16> {
 // change as the values do).  The conversions are sm_100-class
 // cvt.rs.{f16x2,bf16x2}.f32, fed 32 random bits.  Each thread draws one seed
 // per step (sr_seed below): a mixing hash of the raw bits of a few of its
-// pre-collision values and of its position.  The bits of population q are
+// pre-collision (or, in some kernels, post-collision) values and of its
+// position.  The bits of population q are
 // the seed XORed with a distinct constant, one logic operation per stored
 // pair of values.  So the rounding is a fixed function of the state: a step
 // recomputed from the same state (checkpointing) and the in-place scheme
@@ -274,8 +275,9 @@ struct Grid {
 // it).  The rest is O(u^2) plus the non-equilibrium part, an order of
 // magnitude smaller, and so is its rounding.  The corners (|e|^2 = 3) keep
 // (f - w)/w.  J of every pair sits in an FP32 array after the population
-// planes of the buffer, float4 (Jx, Jy, Jz, 0) per pair of the pitched row,
-// 8 bytes per cell; the in-place scheme keeps two such arrays (index 0 for
+// planes of the buffer, float4 (Jx, Jy, Jz, Jx) per pair of the pitched row
+// (Jx twice so that the pairs (Jx, Jy) and (Jz, Jx) are aligned 8-byte
+// loads), 8 bytes per cell; the in-place scheme keeps two such arrays (index 0 for
 // the natural layout, 1 for the swapped one).
 //
 // Who produced a value: the pre-collision f_a(x) is population a of the

@@ -341,6 +341,34 @@ def test_storage_64cubed_500_steps_vs_oracle(lbm, orc, tgv64_oracle, storage, bo
     assert err <= bound
 
 
+@pytest.mark.parametrize("storage,bound", [("f32", 1e-5), ("f16", 1e-3), ("bf16", 1e-3)])
+def test_storage_128cubed_500_steps_vs_oracle_samples(lbm, storage, bound):
+    """The 16-bit storage workload's flow at 128^3 x 500 steps (Taylor-Green
+    + noise, tau = 0.6) against the FP64 oracle's velocity at 1024 sampled
+    cells (tests/golden/tgv128_500_oracle_u.txt, written by
+    make_tgv128_oracle.py, which calls only the oracle): relative L2 over the
+    samples within 1e-5 (FP32 storage) and 1e-3 (FP16, BF16)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "tgv128_500_oracle_u.txt")
+    data = np.loadtxt(path)
+    cells = data[:, 0].astype(np.int64)
+    u_or = data[:, 1:].T
+    Q = 27
+    shape = (128, 128, 128)
+    assert np.array_equal(cells, W.sample_cells(shape, len(cells)))
+    rho0, u0 = W.taylor_green(shape, u0=0.02, noise=1e-3)
+    S = lbm.Solver(Q, shape, W.omegas(Q, 1 / 0.6), storage=storage)
+    S.init_equilibrium(rho0, u0)
+    S.step(500)
+    _, u = S.macroscopic()
+    torch.cuda.synchronize()
+    got = u.reshape(3, -1)[:, torch.as_tensor(cells, device="cuda")].double().cpu().numpy()
+    err = rel_l2(got, u_or)
+    print("%s storage, 128^3 x 500 steps: rel L2 u vs FP64 oracle (1024 cells) = %.3e"
+          % (storage, err))
+    assert err <= bound
+
+
 def test_16bit_storage_512cubed_500_steps_vs_fp32(lbm):
     """The 16-bit storage workload itself (512^3, Taylor-Green + noise,
     tau = 0.6, 500 steps): relative L2 of u of FP16 / BF16 storage against
