@@ -80,7 +80,25 @@ __device__ __forceinline__ void dist_from_central(V u, V k0, V k1, V k2, V &a, V
 
 // Relax the deviation central moments D[m][n][p] (= kappa - kappa^w,
 // source included) in place.  drho = rho - 1.
-template <typename V>
+//
+// kEq: every rate from the trace on (omega_9 .. omega_26) is exactly 1 --
+// the paper's tests and the benchmark relax all but the shear moments at 1.
+// Then c~ = (1 - omega) c + omega c^at is c^at exactly (the FMA of a zero
+// with c adds nothing, and a product with 1 is exact), so those moments are
+// written from their attractors without reading c, and every operation of
+// the forward sweeps that only fed a moment of order >= 3 (or the trace)
+// becomes dead code for the compiler.  The same arithmetic as the general
+// form; the results agree to rounding, not bit for bit, because the code
+// generator fuses some packed multiply-add pairs differently in the two.
+template <bool kEq, typename V>
+__device__ __forceinline__ V relaxed(V omw, V c, V target) {
+    if constexpr (kEq)
+        return target;
+    else
+        return vfma(omw, c, target);
+}
+
+template <typename V, bool kEq = false>
 __device__ __forceinline__ void relax27(V (&D)[3][3][3], V ux, V uy, V uz, V drho,
                                         const Rates27<V> &r) {
     const V third = splat<V>(1.0f / 3.0f), sixth = splat<V>(1.0f / 6.0f);
@@ -102,7 +120,7 @@ __device__ __forceinline__ void relax27(V (&D)[3][3][3], V ux, V uy, V uz, V drh
         const V uxy = ux2 + uy2;
         a = vfma(r.omw[7], a, r.nw[7] * (ux2 - uy2));
         b = vfma(r.omw[8], b, r.nw[8] * (uxy - two * uz2));
-        c = vfma(r.omw[9], c, r.w[9] * (drho - (uxy + uz2)));
+        c = kEq ? drho - (uxy + uz2) : vfma(r.omw[9], c, r.w[9] * (drho - (uxy + uz2)));
         const V c3 = c * third, b6 = b * sixth;
         const V cb = c3 + b6;
         D[2][0][0] = vfma(half, a, cb);
@@ -114,26 +132,26 @@ __device__ __forceinline__ void relax27(V (&D)[3][3][3], V ux, V uy, V uz, V drh
     // order 3: attractors 0; kappa^w_xyy = -u_x Kw_y etc.
     {
         const V s = D[1][2][0] + D[1][0][2], t = D[1][2][0] - D[1][0][2];
-        const V sn = vfma(r.omw[10], s, r.w[10] * (ux * (Kwy + Kwz)));
-        const V tn = vfma(r.omw[13], t, r.w[13] * (ux * (Kwy - Kwz)));
+        const V sn = kEq ? ux * (Kwy + Kwz) : vfma(r.omw[10], s, r.w[10] * (ux * (Kwy + Kwz)));
+        const V tn = kEq ? ux * (Kwy - Kwz) : vfma(r.omw[13], t, r.w[13] * (ux * (Kwy - Kwz)));
         D[1][2][0] = half * (sn + tn);
         D[1][0][2] = half * (sn - tn);
     }
     {
         const V s = D[2][1][0] + D[0][1][2], t = D[2][1][0] - D[0][1][2];
-        const V sn = vfma(r.omw[11], s, r.w[11] * (uy * (Kwx + Kwz)));
-        const V tn = vfma(r.omw[14], t, r.w[14] * (uy * (Kwx - Kwz)));
+        const V sn = kEq ? uy * (Kwx + Kwz) : vfma(r.omw[11], s, r.w[11] * (uy * (Kwx + Kwz)));
+        const V tn = kEq ? uy * (Kwx - Kwz) : vfma(r.omw[14], t, r.w[14] * (uy * (Kwx - Kwz)));
         D[2][1][0] = half * (sn + tn);
         D[0][1][2] = half * (sn - tn);
     }
     {
         const V s = D[2][0][1] + D[0][2][1], t = D[2][0][1] - D[0][2][1];
-        const V sn = vfma(r.omw[12], s, r.w[12] * (uz * (Kwx + Kwy)));
-        const V tn = vfma(r.omw[15], t, r.w[15] * (uz * (Kwx - Kwy)));
+        const V sn = kEq ? uz * (Kwx + Kwy) : vfma(r.omw[12], s, r.w[12] * (uz * (Kwx + Kwy)));
+        const V tn = kEq ? uz * (Kwx - Kwy) : vfma(r.omw[15], t, r.w[15] * (uz * (Kwx - Kwy)));
         D[2][0][1] = half * (sn + tn);
         D[0][2][1] = half * (sn - tn);
     }
-    D[1][1][1] = vfma(r.omw[16], D[1][1][1], r.w[16] * (ux * uy * uz));
+    D[1][1][1] = kEq ? ux * uy * uz : vfma(r.omw[16], D[1][1][1], r.w[16] * (ux * uy * uz));
 
     // order 4: xxyy, xxzz, yyzz -> products of the post-collision kappa~_ii
     {
@@ -142,23 +160,23 @@ __device__ __forceinline__ void relax27(V (&D)[3][3][3], V ux, V uy, V uz, V drh
         const V dC = vfma(Kwy, dzz, vfma(Kwz, dyy, dyy * dzz));
         const V A = D[2][2][0], B = D[2][0][2], C = D[0][2][2];
         const V AB = A + B, dAB = dA + dB;
-        const V p17 = vfma(r.omw[17], AB + C, r.w[17] * (dAB + dC));
-        const V p18 = vfma(r.omw[18], AB - two * C, r.w[18] * (dAB - two * dC));
-        const V p19 = vfma(r.omw[19], A - B, r.w[19] * (dA - dB));
+        const V p17 = kEq ? dAB + dC : vfma(r.omw[17], AB + C, r.w[17] * (dAB + dC));
+        const V p18 = kEq ? dAB - two * dC : vfma(r.omw[18], AB - two * C, r.w[18] * (dAB - two * dC));
+        const V p19 = kEq ? dA - dB : vfma(r.omw[19], A - B, r.w[19] * (dA - dB));
         const V ABn = third * (two * p17 + p18);
         D[0][2][2] = third * (p17 - p18);
         D[2][2][0] = half * (ABn + p19);
         D[2][0][2] = half * (ABn - p19);
     }
     // xxyz, xyyz, xyzz -> 0; kappa^w_xxyz = Kw_x u_y u_z etc.
-    D[2][1][1] = vfma(r.omw[20], D[2][1][1], r.nw[20] * (Kwx * (uy * uz)));
-    D[1][2][1] = vfma(r.omw[21], D[1][2][1], r.nw[21] * (Kwy * (ux * uz)));
-    D[1][1][2] = vfma(r.omw[22], D[1][1][2], r.nw[22] * (Kwz * (ux * uy)));
+    D[2][1][1] = relaxed<kEq>(r.omw[20], D[2][1][1], r.nw[20] * (Kwx * (uy * uz)));
+    D[1][2][1] = relaxed<kEq>(r.omw[21], D[1][2][1], r.nw[21] * (Kwy * (ux * uz)));
+    D[1][1][2] = relaxed<kEq>(r.omw[22], D[1][1][2], r.nw[22] * (Kwz * (ux * uy)));
 
     // order 5 -> 0; kappa^w_xyyzz = -u_x Kw_y Kw_z etc.
-    D[1][2][2] = vfma(r.omw[23], D[1][2][2], r.w[23] * (ux * (Kwy * Kwz)));
-    D[2][1][2] = vfma(r.omw[24], D[2][1][2], r.w[24] * (uy * (Kwx * Kwz)));
-    D[2][2][1] = vfma(r.omw[25], D[2][2][1], r.w[25] * (uz * (Kwx * Kwy)));
+    D[1][2][2] = kEq ? ux * (Kwy * Kwz) : vfma(r.omw[23], D[1][2][2], r.w[23] * (ux * (Kwy * Kwz)));
+    D[2][1][2] = kEq ? uy * (Kwx * Kwz) : vfma(r.omw[24], D[2][1][2], r.w[24] * (uy * (Kwx * Kwz)));
+    D[2][2][1] = kEq ? uz * (Kwx * Kwy) : vfma(r.omw[25], D[2][2][1], r.w[25] * (uz * (Kwx * Kwy)));
 
     // order 6: xxyyzz -> kt_x kt_y kt_z;  kt_x kt_y kt_z - Kw_x Kw_y Kw_z
     {
@@ -166,7 +184,7 @@ __device__ __forceinline__ void relax27(V (&D)[3][3][3], V ux, V uy, V uz, V drh
         // (Kwx + dxx)(Kwy + dyy)(Kwz + dzz) - Kwx Kwy Kwz
         //   = kt_x kt_y dzz + Kwz (kt_x dyy + Kwy dxx)
         const V dK = vfma(ktx * kty, dzz, Kwz * vfma(ktx, dyy, Kwy * dxx));
-        D[2][2][2] = vfma(r.omw[26], D[2][2][2], r.w[26] * dK);
+        D[2][2][2] = kEq ? dK : vfma(r.omw[26], D[2][2][2], r.w[26] * dK);
     }
 }
 
@@ -391,7 +409,7 @@ __device__ __forceinline__ void forward27_w(const V (&s)[27], V (&D)[3][3][3], V
 // kWeighted: inputs are weight-scaled values s and r.omw holds
 // (1 - omega) / 216 (see (2) above).
 // u_out: the velocity (with the F/2 shift) of Eq. velocitycalculation.
-template <typename V, bool kWeighted>
+template <typename V, bool kWeighted, bool kEq = false>
 __device__ __forceinline__ void collide27_g(V (&f)[27], V Fx, V Fy, V Fz, const Rates27<V> &r,
                                             V &ux, V &uy, V &uz) {
     V D[3][3][3];
@@ -403,13 +421,13 @@ __device__ __forceinline__ void collide27_g(V (&f)[27], V Fx, V Fy, V Fz, const 
     D[1][0][0] = D[1][0][0] + Fx;
     D[0][1][0] = D[0][1][0] + Fy;
     D[0][0][1] = D[0][0][1] + Fz;
-    relax27(D, ux, uy, uz, drho, r);
+    relax27<V, kEq>(D, ux, uy, uz, drho, r);
     inverse27_g(D, ux, uy, uz, f);
 }
-template <typename V, bool kWeighted>
+template <typename V, bool kWeighted, bool kEq = false>
 __device__ __forceinline__ void collide27_g(V (&f)[27], V Fx, V Fy, V Fz, const Rates27<V> &r) {
     V ux, uy, uz;
-    collide27_g<V, kWeighted>(f, Fx, Fy, Fz, r, ux, uy, uz);
+    collide27_g<V, kWeighted, kEq>(f, Fx, Fy, Fz, r, ux, uy, uz);
 }
 
 // One cell (or a pair of cells, V = f2): pre-collision deviations in,

@@ -485,13 +485,14 @@ __global__ void __launch_bounds__(128) step_kernel(const StepIO<T> io, const Ste
 // e_x = +-1 sources are two single loads (x0 - 1, x0) or (x0 + 1, x0 + 2).
 // Blocks of 128 per SM, by measurement: FP32 storage 5 (96 registers, no
 // spills; 6 blocks ran the same, 32.20k vs 32.23k MLUPS at 256^3, and 7
-// slower); FP16 storage 6 (80 registers, 64 bytes of spills): 41.2k / 44.3k
-// / 37.5k MLUPS at 5 / 6 / 7 blocks at 512^3; BF16 (with its reference
-// loads) 5: 38.1k / 37.0k / 32.0k.
+// slower); 16-bit storage 6 (80 registers): with the rate-1 relaxation FP16
+// 48.2k / 48.0k MLUPS at 6 / 7 blocks at 512^3 (before it 41.2k / 44.3k /
+// 37.5k at 5 / 6 / 7), BF16 with its reference loads 38.6k / 39.4k at 5 / 6.
 template <typename T>
-constexpr int kStep2Blocks = Storage<T>::kRef ? 5 : Storage<T>::kScaled ? 6 : 5;
+constexpr int kStep2Blocks = Storage<T>::kScaled ? 6 : 5;
 
-template <typename T, bool kWalls>
+// kEq: the rates from the trace on are all 1 (relax27).
+template <typename T, bool kWalls, bool kEq>
 __global__ void __launch_bounds__(128, kStep2Blocks<T>) step2_kernel(const StepIO<T> io,
                                                                   const StepArgs a,
                                                                   const PackedRates pr) {
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(128, kStep2Blocks<T>) step2_kernel(const StepI
     }
     const Rates27<f2> r = load_rates_packed(pr);
     f2 ux, uy, uz;
-    collide27_g<f2, Storage<T>::kScaled>(f, Fx, Fy, Fz, r, ux, uy, uz);
+    collide27_g<f2, Storage<T>::kScaled, kEq>(f, Fx, Fy, Fz, r, ux, uy, uz);
     float4 J = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if constexpr (Storage<T>::kRef) {
         J = pair_ref(ux, uy, uz);
@@ -639,17 +640,17 @@ template <int Q>
 struct PairCollide;
 template <>
 struct PairCollide<27> {
-    template <bool kWeighted>
+    template <bool kWeighted, bool kEq>
     __device__ __forceinline__ static void run(f2 (&f)[27], f2 Fx, f2 Fy, f2 Fz,
                                                const PackedRates &pr, bool, f2 &ux, f2 &uy,
                                                f2 &uz) {
         const Rates27<f2> r = load_rates_packed(pr);
-        collide27_g<f2, kWeighted>(f, Fx, Fy, Fz, r, ux, uy, uz);
+        collide27_g<f2, kWeighted, kEq>(f, Fx, Fy, Fz, r, ux, uy, uz);
     }
 };
 template <>
 struct PairCollide<15> {
-    template <bool>
+    template <bool, bool>
     __device__ __forceinline__ static void run(f2 (&f)[15], f2 Fx, f2 Fy, f2 Fz,
                                                const PackedRates &pr, bool has_force, f2 &ux,
                                                f2 &uy, f2 &uz) {
@@ -689,14 +690,14 @@ __device__ __forceinline__ void pair_inputs(const StepIO<T> &io, const Rows<kWal
 }
 
 // The collision of an in-place step, then the pair's reference (BF16).
-template <int Q, typename T>
+template <int Q, typename T, bool kEq>
 __device__ __forceinline__ float4 pair_collide(const StepIO<T> &io, const StepArgs &a,
                                                const PackedRates &pr, int x0, int y, int z,
                                                int own, f2 (&f)[Q]) {
     f2 Fx, Fy, Fz, ux, uy, uz;
     pair_force(a, x0, y, z, Fx, Fy, Fz);
-    PairCollide<Q>::template run<kFoldedLoad<Q, T>()>(f, Fx, Fy, Fz, pr, a.has_force != 0, ux,
-                                                      uy, uz);
+    PairCollide<Q>::template run<kFoldedLoad<Q, T>(), kEq>(f, Fx, Fy, Fz, pr, a.has_force != 0,
+                                                           ux, uy, uz);
     float4 J = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if constexpr (Storage<T>::kRef) {
         J = pair_ref(ux, uy, uz);
@@ -705,7 +706,7 @@ __device__ __forceinline__ float4 pair_collide(const StepIO<T> &io, const StepAr
     return J;
 }
 
-template <int Q, typename T, bool kWalls>
+template <int Q, typename T, bool kWalls, bool kEq>
 __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const StepArgs a,
                                                       const PackedRates pr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -724,7 +725,7 @@ __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const 
     pair_inputs<Q, T, kWalls>(io, R, x0, xm, xp, f);
     unsigned seed = 0;
     if constexpr (!kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
-    const float4 J = pair_collide<Q, T>(io, a, pr, x0, y, z, own, f);
+    const float4 J = pair_collide<Q, T, kEq>(io, a, pr, x0, y, z, own, f);
     if constexpr (kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
@@ -739,7 +740,7 @@ __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const 
 template <int Q, typename T>
 constexpr int kAAOddBlocks = Q == 27 ? 5 : 4;
 
-template <int Q, typename T, bool kWalls>
+template <int Q, typename T, bool kWalls, bool kEq>
 __global__ void __launch_bounds__(128, (kAAOddBlocks<Q, T>))
     aa_odd_kernel(const StepIO<T> io, const StepArgs a, const PackedRates pr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -772,7 +773,7 @@ __global__ void __launch_bounds__(128, (kAAOddBlocks<Q, T>))
     pair_inputs<Q, T, kWalls>(io, R, x0, xm, xp, f);
     unsigned seed = 0;
     if constexpr (!kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
-    const float4 J = pair_collide<Q, T>(io, a, pr, x0, y, z, own, f);
+    const float4 J = pair_collide<Q, T, kEq>(io, a, pr, x0, y, z, own, f);
     if constexpr (kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
@@ -985,6 +986,16 @@ inline PackedRates packed_rates(const StepArgs &a, bool weighted = false) {
     return p;
 }
 
+// D3Q27: the rates from the trace on (omega_9 .. omega_26) are all exactly
+// 1, the paper's choice for every non-shear moment, so the pair kernels can
+// take the kEq form of the relaxation (relax27: the same arithmetic, with
+// the work that only fed those moments dropped).
+inline bool higher_rates_are_one(const StepArgs &a) {
+    for (int b = 9; b < 27; ++b)
+        if (a.w[b] != 1.0f) return false;
+    return true;
+}
+
 // The two-cells-per-thread kernels serve grids with even nx (D3Q27 and
 // D3Q15); odd nx takes the one-cell kernel.
 template <int Q, typename T>
@@ -1013,10 +1024,15 @@ cudaError_t launch_step(const void *fin, void *fout, const StepArgs &a, cudaStre
             half.nx = a.g.nx / 2;
             const CellLaunch L = cell_launch(half);
             const PackedRates pr = packed_rates(a, kFoldedLoad<27, T>());
-            if (walls)
-                step2_kernel<T, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+            const bool eq = higher_rates_are_one(a);
+            if (walls && eq)
+                step2_kernel<T, true, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+            else if (walls)
+                step2_kernel<T, true, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
+            else if (eq)
+                step2_kernel<T, false, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
             else
-                step2_kernel<T, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
+                step2_kernel<T, false, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
             return cudaGetLastError();
         }
     } else {
@@ -1060,14 +1076,25 @@ cudaError_t launch_step_aa(void *buf, const StepArgs &a, bool even, cudaStream_t
     half.nx = a.g.nx / 2;
     const CellLaunch L = cell_launch(half);
     const PackedRates pr = packed_rates(a, kFoldedLoad<Q, T>());
+    if (Q == 27 && higher_rates_are_one(a)) {
+        if (even && a.g.bc)
+            aa_even_kernel<Q, T, true, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+        else if (even)
+            aa_even_kernel<Q, T, false, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+        else if (a.g.bc)
+            aa_odd_kernel<Q, T, true, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+        else
+            aa_odd_kernel<Q, T, false, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+        return cudaGetLastError();
+    }
     if (even && a.g.bc)
-        aa_even_kernel<Q, T, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+        aa_even_kernel<Q, T, true, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
     else if (even)
-        aa_even_kernel<Q, T, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
+        aa_even_kernel<Q, T, false, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
     else if (a.g.bc)
-        aa_odd_kernel<Q, T, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+        aa_odd_kernel<Q, T, true, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
     else
-        aa_odd_kernel<Q, T, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
+        aa_odd_kernel<Q, T, false, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
     return cudaGetLastError();
 }
 

@@ -424,6 +424,33 @@ def test_stochastically_rounded_fp32_update_matches_oracle(lbm, orc, Q, bc, shap
     assert np.array_equal(runs[0], runs[1])
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("inplace", [False, True])
+def test_rates_of_one_form_equals_general_form(lbm, storage, inplace):
+    """With every rate from the trace on exactly 1 the D3Q27 pair kernels
+    take the rate-1 form of the relaxation (the attractors written without
+    reading the pre-collision moments).  Against the general form, forced by
+    omega_26 = the float just below 1, the states after 20 steps agree to
+    rounding and the tiny effect of that rate difference (walls, force
+    field)."""
+    shape = (6, 10, 16)
+    rng = W.rng(91)
+    F = rng.uniform(-2e-4, 2e-4, (3,) + shape).astype(np.float32).astype(np.float64)
+    rho0, u0 = W.taylor_green(shape, u0=0.04, noise=2e-3)
+    om = W.omegas(27, 1 / 0.55)
+    om_gen = om.copy()
+    om_gen[26] = float(np.nextafter(np.float32(1.0), np.float32(0.0)))
+    states = []
+    for o in (om, om_gen):
+        S = lbm.Solver(27, shape, o, force=F, walls=3, storage=storage, inplace=inplace)
+        S.init_equilibrium(rho0, u0)
+        S.step(20)
+        states.append(gpu_state(S))
+    # FP32: the forms agree to rounding; 16-bit: a value the two forms put a
+    # rounding error apart can be stored one 16-bit unit apart (<= ~1e-5 in f)
+    assert np.abs(states[0] - states[1]).max() <= (1e-7 if storage == "f32" else 1e-4)
+
+
 @pytest.mark.parametrize("tau", [0.51, 1.0])
 def test_tau_sweep_extremes_64cubed_100_steps(lbm, orc, tau):
     """The tau sweep's workload (D3Q27 Taylor-Green + noise, periodic, FP32
