@@ -186,13 +186,30 @@ struct StepIO {
 // 2-cell pair helpers for the packed kernel (x0 even, row pitch even).
 template <typename T>
 struct Pair;
+// State loads: read-only, with an L2 prefetch-size hint of 256 bytes (the
+// pulls stream through whole rows; measured +2.4 % FP16, +1.5 % BF16 at
+// 512^3, FP32 unchanged).
+__device__ __forceinline__ unsigned long long ld_nc_256_b64(const void *p) {
+    unsigned long long v;
+    asm("ld.global.nc.L2::256B.b64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned ld_nc_256_b32(const void *p) {
+    unsigned v;
+    asm("ld.global.nc.L2::256B.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned short ld_nc_256_b16(const void *p) {
+    unsigned short v;
+    asm("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
 template <>
 struct Pair<float> {
-    __device__ __forceinline__ static f2 ld2(const float *p) {
-        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
-        return f2(v.x, v.y);
+    __device__ __forceinline__ static f2 ld2(const float *p) { return f2(ld_nc_256_b64(p)); }
+    __device__ __forceinline__ static float ld1(const float *p) {
+        return __uint_as_float(ld_nc_256_b32(p));
     }
-    __device__ __forceinline__ static float ld1(const float *p) { return __ldg(p); }
     __device__ __forceinline__ static void st2(float *p, f2 v) {
         __stcs(reinterpret_cast<float2 *>(p), make_float2(v.lo(), v.hi()));
     }
@@ -225,21 +242,23 @@ struct Pair16 {
 template <>
 struct Pair<__half> : Pair16<__half> {
     __device__ __forceinline__ static f2 ld2(const __half *p) {
-        const float2 v = __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
+        const unsigned w = ld_nc_256_b32(p);
+        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(&w));
         return f2(v.x, v.y);
     }
     __device__ __forceinline__ static float ld1(const __half *p) {
-        return __half2float(__ldg(p));
+        return __half2float(__ushort_as_half(ld_nc_256_b16(p)));
     }
 };
 template <>
 struct Pair<__nv_bfloat16> : Pair16<__nv_bfloat16> {
     __device__ __forceinline__ static f2 ld2(const __nv_bfloat16 *p) {
-        const float2 v = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
+        const unsigned w = ld_nc_256_b32(p);
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
         return f2(v.x, v.y);
     }
     __device__ __forceinline__ static float ld1(const __nv_bfloat16 *p) {
-        return __bfloat162float(__ldg(p));
+        return __bfloat162float(__ushort_as_bfloat16(ld_nc_256_b16(p)));
     }
 };
 
