@@ -40,41 +40,8 @@ __device__ __forceinline__ void adjoint15(const V (&f)[15], V Fx, V Fy, V Fz,
     const V third = splat<V>(1.0f / 3.0f), six = splat<V>(6.0f);
 
     // ---- forward recomputation (the quantities of kernels15)
-    V drho = zero, jx = zero, jy = zero, jz = zero;
-    V kxy = zero, kxz = zero, kyz = zero, kxx = zero, kyy = zero, kzz = zero;
-    V kxyy = zero, kxxy = zero, kxxz = zero, kxyz = zero, kxxyy = zero;
-    static_for<15>([&](auto ia) {
-        constexpr int a = decltype(ia)::value;
-        constexpr int x = q15_e(a, 0), y = q15_e(a, 1), z = q15_e(a, 2);
-        const V v = f[a];
-        drho = drho + v;
-        if constexpr (x > 0) jx = jx + v;
-        if constexpr (x < 0) jx = jx - v;
-        if constexpr (y > 0) jy = jy + v;
-        if constexpr (y < 0) jy = jy - v;
-        if constexpr (z > 0) jz = jz + v;
-        if constexpr (z < 0) jz = jz - v;
-        if constexpr (x != 0) kxx = kxx + v;
-        if constexpr (y != 0) kyy = kyy + v;
-        if constexpr (z != 0) kzz = kzz + v;
-        if constexpr (x * y * z != 0) {
-            kxxyy = kxxyy + v;
-            if constexpr (x * y > 0) kxy = kxy + v;
-            if constexpr (x * y < 0) kxy = kxy - v;
-            if constexpr (x * z > 0) kxz = kxz + v;
-            if constexpr (x * z < 0) kxz = kxz - v;
-            if constexpr (y * z > 0) kyz = kyz + v;
-            if constexpr (y * z < 0) kyz = kyz - v;
-            if constexpr (x > 0) kxyy = kxyy + v;
-            if constexpr (x < 0) kxyy = kxyy - v;
-            if constexpr (y > 0) kxxy = kxxy + v;
-            if constexpr (y < 0) kxxy = kxxy - v;
-            if constexpr (z > 0) kxxz = kxxz + v;
-            if constexpr (z < 0) kxxz = kxxz - v;
-            if constexpr (x * y * z > 0) kxyz = kxyz + v;
-            if constexpr (x * y * z < 0) kxyz = kxyz - v;
-        }
-    });
+    V drho, jx, jy, jz, kxy, kxz, kyz, kxx, kyy, kzz, kxyy, kxxy, kxxz, kxyz, kxxyy;
+    sums15(f, drho, jx, jy, jz, kxy, kxz, kyz, kxx, kyy, kzz, kxyy, kxxy, kxxz, kxyz, kxxyy);
     const V rho = one + drho;
     const V inv_rho = vrcp(rho);
     const V ux = vfma(half, Fx, jx) * inv_rho;
@@ -116,19 +83,32 @@ __device__ __forceinline__ void adjoint15(const V (&f)[15], V Fx, V Fy, V Fz,
     const V dky = vfma(six, g[9], eyy + two * (g[8] - g[7])) - vfma(rho, uy2, fuy);
 
     // ---- reverse of the update: projections of mu on the basis
+    // On the corners the basis vectors are 1 (K0, K9), 2 (K14), sx, sy, sz
+    // (K1..K3, and K10..K12 times 2), sx sy, sx sz, sy sz (K4..K6),
+    // sx sy sz (K13), and 0 (K7, K8); on the axis pairs K9 = -1, K14 = -8,
+    // K10..K12 = -8 e; at rest K9 = -2, K14 = 32 (k15 above).
     V P[15];
-    static_for<15>([&](auto ib) {
-        constexpr int b = decltype(ib)::value;
-        V s = zero;
-        static_for<15>([&](auto ia) {
-            constexpr int a = decltype(ia)::value;
-            constexpr int k = k15(b, a);
-            if constexpr (k == 1) s = s + mu[a];
-            else if constexpr (k == -1) s = s - mu[a];
-            else if constexpr (k != 0) s = vfma(splat<V>(float(k)), mu[a], s);
-        });
-        P[b] = s;
-    });
+    {
+        V Cm, Cx, Cy, Cz, Cxy, Cxz, Cyz, Cxyz, sm, dx, dy, dz, ax, ay, az;
+        corner_axis_sums15(mu, Cm, Cx, Cy, Cz, Cxy, Cxz, Cyz, Cxyz, ax, ay, az, dx, dy, dz);
+        sm = (ax + ay) + az;
+        const V m8 = splat<V>(-8.0f);
+        P[0] = (mu[0] + sm) + Cm;
+        P[1] = dx + Cx;
+        P[2] = dy + Cy;
+        P[3] = dz + Cz;
+        P[4] = Cxy;
+        P[5] = Cxz;
+        P[6] = Cyz;
+        P[7] = ax - ay;
+        P[8] = (ax + ay) - two * az;
+        P[9] = vfma(splat<V>(-2.0f), mu[0], Cm - sm);
+        P[10] = vfma(m8, dx, two * Cx);
+        P[11] = vfma(m8, dy, two * Cy);
+        P[12] = vfma(m8, dz, two * Cz);
+        P[13] = Cxyz;
+        P[14] = vfma(splat<V>(32.0f), mu[0], vfma(m8, sm, two * Cm));
+    }
     V bg[15];
 #pragma unroll
     for (int b = 4; b < 15; ++b) bg[b] = P[b];
@@ -478,38 +458,43 @@ __device__ __forceinline__ void adjoint15(const V (&f)[15], V Fx, V Fy, V Fz,
     b_rho = b_rho - vfma(ux, b_jx, vfma(uy, b_jy, uz * b_jz));
     b_drho = b_drho + b_rho;
     // ---- the sums, transposed: lam = mu + sum_s (d s / d f) sbar
-    static_for<15>([&](auto ia) {
-        constexpr int a = decltype(ia)::value;
-        constexpr int x = q15_e(a, 0), y = q15_e(a, 1), z = q15_e(a, 2);
-        V v = mu[a] + b_drho;
-        if constexpr (x > 0) v = v + b_jx;
-        if constexpr (x < 0) v = v - b_jx;
-        if constexpr (y > 0) v = v + b_jy;
-        if constexpr (y < 0) v = v - b_jy;
-        if constexpr (z > 0) v = v + b_jz;
-        if constexpr (z < 0) v = v - b_jz;
-        if constexpr (x != 0) v = v + b_exx;  // d exx / d kxx = 1
-        if constexpr (y != 0) v = v + b_eyy;
-        if constexpr (z != 0) v = v + b_ezz;
-        if constexpr (x * y * z != 0) {
-            v = v + b_exxyy;
-            if constexpr (x * y > 0) v = v + b_exy;
-            if constexpr (x * y < 0) v = v - b_exy;
-            if constexpr (x * z > 0) v = v + b_exz;
-            if constexpr (x * z < 0) v = v - b_exz;
-            if constexpr (y * z > 0) v = v + b_eyz;
-            if constexpr (y * z < 0) v = v - b_eyz;
-            if constexpr (x > 0) v = v + b_exyy;
-            if constexpr (x < 0) v = v - b_exyy;
-            if constexpr (y > 0) v = v + b_exxy;
-            if constexpr (y < 0) v = v - b_exxy;
-            if constexpr (z > 0) v = v + b_exxz;
-            if constexpr (z < 0) v = v - b_exxz;
-            if constexpr (x * y * z > 0) v = v + b_exyz;
-            if constexpr (x * y * z < 0) v = v - b_exyz;
-        }
-        lam[a] = v;
-    });
+    // each lam_a = mu_a + sum over the sums s of (d s / d f_a) sbar: on the
+    // corners a sign pattern of 8 coefficients (a butterfly, as in update15)
+    {
+        const V ex = b_drho + b_exx, ey = b_drho + b_eyy, ez = b_drho + b_ezz;
+        lam[0] = mu[0] + b_drho;
+        static_for<6>([&](auto ia) {
+            constexpr int a = 1 + decltype(ia)::value;
+            constexpr int x = q15_e(a, 0), y = q15_e(a, 1), z = q15_e(a, 2);
+            V v;
+            if constexpr (x > 0) v = ex + b_jx;
+            if constexpr (x < 0) v = ex - b_jx;
+            if constexpr (y > 0) v = ey + b_jy;
+            if constexpr (y < 0) v = ey - b_jy;
+            if constexpr (z > 0) v = ez + b_jz;
+            if constexpr (z < 0) v = ez - b_jz;
+            lam[a] = mu[a] + v;
+        });
+        const V c0 = ((ex + b_eyy) + (b_ezz + b_exxyy));
+        const V cx = b_jx + b_exyy, cy = b_jy + b_exxy, cz = b_jz + b_exxz;
+        V A[2], Bx[2], By[2], Bxy[2];
+        A[0] = c0 + cz;
+        A[1] = c0 - cz;
+        Bx[0] = cx + b_exz;
+        Bx[1] = cx - b_exz;
+        By[0] = cy + b_eyz;
+        By[1] = cy - b_eyz;
+        Bxy[0] = b_exy + b_exyz;
+        Bxy[1] = b_exy - b_exyz;
+        static_for<8>([&](auto ic) {
+            constexpr int a = 7 + decltype(ic)::value;
+            constexpr int x = q15_e(a, 0), y = q15_e(a, 1), z = q15_e(a, 2);
+            constexpr int k = z > 0 ? 0 : 1;
+            const V P2 = y > 0 ? A[k] + By[k] : A[k] - By[k];
+            const V R2 = y > 0 ? Bx[k] + Bxy[k] : Bx[k] - Bxy[k];
+            lam[a] = mu[a] + (x > 0 ? P2 + R2 : P2 - R2);
+        });
+    }
 }
 
 }  // namespace lbm

@@ -94,44 +94,69 @@ __device__ __forceinline__ void source_projections15(V Fx, V Fy, V Fz, V ux, V u
                                         fuz * vfma(three, ux2 + uy2, m4)));
 }
 
+// The 8 sign-pattern sums over the corners (sx, sy, sz) of v: sum of v,
+// of sx v, sy v, sz v, sx sy v, sx sz v, sy sz v and sx sy sz v, as a
+// three-level butterfly (24 additions instead of 8 per pattern); and the
+// axis pairs as sums a_i = v(+e_i) + v(-e_i) and differences d_i.
+template <typename V>
+__device__ __forceinline__ void corner_axis_sums15(const V (&v)[15], V &C, V &Cx, V &Cy, V &Cz,
+                                                   V &Cxy, V &Cxz, V &Cyz, V &Cxyz, V &ax, V &ay,
+                                                   V &az, V &dx, V &dy, V &dz) {
+    // level 1 over sz: S/D[i][j] at sx = i ? -1 : +1, sy = j ? -1 : +1
+    V S[2][2], D[2][2];
+    static_for<4>([&](auto ij) {
+        constexpr int i = decltype(ij)::value >> 1, j = decltype(ij)::value & 1;
+        constexpr int sx = i ? -1 : 1, sy = j ? -1 : 1;
+        const V up = v[slot_of<15>(sx, sy, 1)], dn = v[slot_of<15>(sx, sy, -1)];
+        S[i][j] = up + dn;
+        D[i][j] = up - dn;
+    });
+    // level 2 over sy: patterns 1, sy, sz, sy sz at sx = +1 (index 0) and -1
+    V c1[2], cy[2], cz[2], cyz[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        c1[i] = S[i][0] + S[i][1];
+        cy[i] = S[i][0] - S[i][1];
+        cz[i] = D[i][0] + D[i][1];
+        cyz[i] = D[i][0] - D[i][1];
+    }
+    // level 3 over sx
+    C = c1[0] + c1[1];
+    Cx = c1[0] - c1[1];
+    Cy = cy[0] + cy[1];
+    Cxy = cy[0] - cy[1];
+    Cz = cz[0] + cz[1];
+    Cxz = cz[0] - cz[1];
+    Cyz = cyz[0] + cyz[1];
+    Cxyz = cyz[0] - cyz[1];
+    constexpr int px = slot_of<15>(1, 0, 0), mx = slot_of<15>(-1, 0, 0);
+    constexpr int py = slot_of<15>(0, 1, 0), my = slot_of<15>(0, -1, 0);
+    constexpr int pz = slot_of<15>(0, 0, 1), mz = slot_of<15>(0, 0, -1);
+    ax = v[px] + v[mx];
+    ay = v[py] + v[my];
+    az = v[pz] + v[mz];
+    dx = v[px] - v[mx];
+    dy = v[py] - v[my];
+    dz = v[pz] - v[mz];
+}
+
 // Signed sums of the deviations over the index sets of App. G (the raw
-// moments the cascade needs), accumulated onto the given values.
+// moments the cascade needs).  D3Q15 has no xy, xz or yz edges, so every
+// mixed moment lives on the corners alone and is one sign pattern there.
 template <typename V>
 __device__ __forceinline__ void sums15(const V (&f)[15], V &drho, V &jx, V &jy, V &jz, V &kxy,
                                        V &kxz, V &kyz, V &kxx, V &kyy, V &kzz, V &kxyy, V &kxxy,
                                        V &kxxz, V &kxyz, V &kxxyy) {
-    static_for<15>([&](auto ia) {
-        constexpr int a = decltype(ia)::value;
-        constexpr int x = q15_e(a, 0), y = q15_e(a, 1), z = q15_e(a, 2);
-        const V v = f[a];
-        drho = drho + v;
-        if constexpr (x > 0) jx = jx + v;
-        if constexpr (x < 0) jx = jx - v;
-        if constexpr (y > 0) jy = jy + v;
-        if constexpr (y < 0) jy = jy - v;
-        if constexpr (z > 0) jz = jz + v;
-        if constexpr (z < 0) jz = jz - v;
-        if constexpr (x != 0) kxx = kxx + v;
-        if constexpr (y != 0) kyy = kyy + v;
-        if constexpr (z != 0) kzz = kzz + v;
-        if constexpr (x * y * z != 0) {  // corners
-            kxxyy = kxxyy + v;
-            if constexpr (x * y > 0) kxy = kxy + v;
-            if constexpr (x * y < 0) kxy = kxy - v;
-            if constexpr (x * z > 0) kxz = kxz + v;
-            if constexpr (x * z < 0) kxz = kxz - v;
-            if constexpr (y * z > 0) kyz = kyz + v;
-            if constexpr (y * z < 0) kyz = kyz - v;
-            if constexpr (x > 0) kxyy = kxyy + v;
-            if constexpr (x < 0) kxyy = kxyy - v;
-            if constexpr (y > 0) kxxy = kxxy + v;
-            if constexpr (y < 0) kxxy = kxxy - v;
-            if constexpr (z > 0) kxxz = kxxz + v;
-            if constexpr (z < 0) kxxz = kxxz - v;
-            if constexpr (x * y * z > 0) kxyz = kxyz + v;
-            if constexpr (x * y * z < 0) kxyz = kxyz - v;
-        }
-    });
+    V C, ax, ay, az, dx, dy, dz;
+    corner_axis_sums15(f, C, kxyy, kxxy, kxxz, kxy, kxz, kyz, kxyz, ax, ay, az, dx, dy, dz);
+    kxxyy = C;
+    jx = dx + kxyy;
+    jy = dy + kxxy;
+    jz = dz + kxxz;
+    kxx = ax + C;
+    kyy = ay + C;
+    kzz = az + C;
+    drho = ((f[0] + C) + ax) + (ay + az);
 }
 
 // The cascade on deviation raw moments; returns u and g[4..14].  The rates
@@ -140,9 +165,7 @@ template <typename V>
 __device__ __forceinline__ void kernels15(const V (&f)[15], V Fx, V Fy, V Fz, const Rates15<V> &r,
                                           V &ux, V &uy, V &uz, V (&g)[15]) {
     const V zero = splat<V>(0.0f);
-    V drho = zero, jx = zero, jy = zero, jz = zero;
-    V kxy = zero, kxz = zero, kyz = zero, kxx = zero, kyy = zero, kzz = zero;
-    V kxyy = zero, kxxy = zero, kxxz = zero, kxyz = zero, kxxyy = zero;
+    V drho, jx, jy, jz, kxy, kxz, kyz, kxx, kyy, kzz, kxyy, kxxy, kxxz, kxyz, kxxyy;
     sums15(f, drho, jx, jy, jz, kxy, kxz, kyz, kxx, kyy, kzz, kxyy, kxxy, kxxz, kxyz, kxxyy);
     const V one = splat<V>(1.0f), half = splat<V>(0.5f), two = splat<V>(2.0f);
     const V three = splat<V>(3.0f), eighth = splat<V>(0.125f);
@@ -221,9 +244,7 @@ template <typename V>
 __device__ __forceinline__ void kernels15_unforced(const V (&f)[15], const Rates15<V> &r, V &ux,
                                                    V &uy, V &uz, V (&g)[15]) {
     const V zero = splat<V>(0.0f);
-    V drho = zero, jx = zero, jy = zero, jz = zero;
-    V kxy = zero, kxz = zero, kyz = zero, kxx = zero, kyy = zero, kzz = zero;
-    V kxyy = zero, kxxy = zero, kxxz = zero, kxyz = zero, kxxyy = zero;
+    V drho, jx, jy, jz, kxy, kxz, kyz, kxx, kyy, kzz, kxyy, kxxy, kxxz, kxyz, kxxyy;
     sums15(f, drho, jx, jy, jz, kxy, kxz, kyz, kxx, kyy, kzz, kxyy, kxxy, kxxz, kxyz, kxxyy);
     const V one = splat<V>(1.0f), two = splat<V>(2.0f);
     const V three = splat<V>(3.0f), eighth = splat<V>(0.125f), third = splat<V>(1.0f / 3.0f);
