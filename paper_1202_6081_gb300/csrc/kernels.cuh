@@ -582,16 +582,37 @@ __device__ __forceinline__ f2 pull_pair(const StepIO<T> &io, const Rows<kWalls> 
     return f2(Pair<T>::ld1(row + x0 + 1), Pair<T>::ld1(row + xp));
 }
 
+// Body force of the pair (x0, x0 + 1): the field, else the uniform force.
+__device__ __forceinline__ void pair_force(const StepArgs &a, int x0, int y, int z, f2 &Fx, f2 &Fy,
+                                           f2 &Fz) {
+    if (a.Ffield) {
+        const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
+        const long long c = dense_index(a.g, x0, y, z);
+        Fx = f2(__ldg(a.Ffield + c), __ldg(a.Ffield + c + 1));
+        Fy = f2(__ldg(a.Ffield + N + c), __ldg(a.Ffield + N + c + 1));
+        Fz = f2(__ldg(a.Ffield + 2 * N + c), __ldg(a.Ffield + 2 * N + c + 1));
+    } else {
+        Fx = f2(a.F[0]);
+        Fy = f2(a.F[1]);
+        Fz = f2(a.F[2]);
+    }
+}
+
 // One fused D3Q15 step, two neighbouring cells per thread in packed f32x2
 // arithmetic (nx even); loads and stores as in step2_kernel.
-// 16-bit storage: 5 blocks per SM (a few spilled registers) beat 4 (60.2k
-// vs 55.4k MLUPS at 256^3); FP32 storage is faster at 4 without spills.
-template <typename T>
-constexpr int kQ15Blocks = Storage<T>::kScaled ? 5 : 4;
+// kForce = false (no force anywhere) compiles the force-free cascade alone:
+// without the forced path beside it the kernel needs fewer registers (no
+// spills at 5 blocks per SM with 16-bit storage, against 104-128 bytes;
+// FP16 77.2k against 70.7k MLUPS at 256^3).  Blocks per SM with 16-bit
+// storage, from measurement: 6 without force (32-56 bytes of spills; FP16
+// 79.2k MLUPS, 78.2k at 7), 5 with it; FP32 storage 4 (no spills; without
+// force its 94 registers admit 5).
+template <typename T, bool kForce>
+constexpr int kQ15Blocks = Storage<T>::kScaled ? (kForce ? 5 : 6) : 4;
 
-template <typename T, bool kWalls>
-__global__ void __launch_bounds__(128, kQ15Blocks<T>) step2_q15_kernel(const StepIO<T> io, const StepArgs a,
-                                                        const PackedRates pr) {
+template <typename T, bool kWalls, bool kForce>
+__global__ void __launch_bounds__(128, (kQ15Blocks<T, kForce>))
+    step2_q15_kernel(const StepIO<T> io, const StepArgs a, const PackedRates pr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
     const int x0 = 2 * t;
@@ -613,23 +634,13 @@ __global__ void __launch_bounds__(128, kQ15Blocks<T>) step2_q15_kernel(const Ste
     }
     unsigned seed = 0;
     if constexpr (!kSeedAfterCollision<15, T>) seed = pair_seed<15>(f, R.own + x0);
-    f2 Fx, Fy, Fz;
-    if (a.Ffield) {
-        const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
-        const long long c = dense_index(a.g, x0, y, z);
-        Fx = f2(__ldg(a.Ffield + c), __ldg(a.Ffield + c + 1));
-        Fy = f2(__ldg(a.Ffield + N + c), __ldg(a.Ffield + N + c + 1));
-        Fz = f2(__ldg(a.Ffield + 2 * N + c), __ldg(a.Ffield + 2 * N + c + 1));
-    } else {
-        Fx = f2(a.F[0]);
-        Fy = f2(a.F[1]);
-        Fz = f2(a.F[2]);
-    }
+    f2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
+    if constexpr (kForce) pair_force(a, x0, y, z, Fx, Fy, Fz);
     Rates15<f2> r;
 #pragma unroll
     for (int b = 0; b < 15; ++b) r.w[b] = f2(pr.w15[b]);
     f2 ux, uy, uz;
-    collide15<f2>(f, Fx, Fy, Fz, r, a.has_force != 0, ux, uy, uz);
+    collide15<f2>(f, Fx, Fy, Fz, r, kForce, ux, uy, uz);
     float4 J = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if constexpr (Storage<T>::kRef) {
         J = pair_ref(ux, uy, uz);
@@ -657,43 +668,28 @@ __global__ void __launch_bounds__(128, kQ15Blocks<T>) step2_q15_kernel(const Ste
 
 template <int Q>
 struct PairCollide;
+// kForce = false: no force anywhere (D3Q15 then takes the force-free
+// cascade; the D3Q27 collision takes any force, zero included, the same way).
 template <>
 struct PairCollide<27> {
-    template <bool kWeighted, bool kEq>
+    template <bool kWeighted, bool kEq, bool>
     __device__ __forceinline__ static void run(f2 (&f)[27], f2 Fx, f2 Fy, f2 Fz,
-                                               const PackedRates &pr, bool, f2 &ux, f2 &uy,
-                                               f2 &uz) {
+                                               const PackedRates &pr, f2 &ux, f2 &uy, f2 &uz) {
         const Rates27<f2> r = load_rates_packed(pr);
         collide27_g<f2, kWeighted, kEq>(f, Fx, Fy, Fz, r, ux, uy, uz);
     }
 };
 template <>
 struct PairCollide<15> {
-    template <bool, bool>
+    template <bool, bool, bool kForce>
     __device__ __forceinline__ static void run(f2 (&f)[15], f2 Fx, f2 Fy, f2 Fz,
-                                               const PackedRates &pr, bool has_force, f2 &ux,
-                                               f2 &uy, f2 &uz) {
+                                               const PackedRates &pr, f2 &ux, f2 &uy, f2 &uz) {
         Rates15<f2> r;
 #pragma unroll
         for (int b = 0; b < 15; ++b) r.w[b] = f2(pr.w15[b]);
-        collide15<f2>(f, Fx, Fy, Fz, r, has_force, ux, uy, uz);
+        collide15<f2>(f, Fx, Fy, Fz, r, kForce, ux, uy, uz);
     }
 };
-
-__device__ __forceinline__ void pair_force(const StepArgs &a, int x0, int y, int z, f2 &Fx, f2 &Fy,
-                                           f2 &Fz) {
-    if (a.Ffield) {
-        const long long N = (long long)a.g.nx * a.g.ny * a.g.nz;
-        const long long c = dense_index(a.g, x0, y, z);
-        Fx = f2(__ldg(a.Ffield + c), __ldg(a.Ffield + c + 1));
-        Fy = f2(__ldg(a.Ffield + N + c), __ldg(a.Ffield + N + c + 1));
-        Fz = f2(__ldg(a.Ffield + 2 * N + c), __ldg(a.Ffield + 2 * N + c + 1));
-    } else {
-        Fx = f2(a.F[0]);
-        Fy = f2(a.F[1]);
-        Fz = f2(a.F[2]);
-    }
-}
 
 // Raw pulled values -> the collision's inputs: BF16 references added (their
 // producers are the pull sources, see lattice.cuh), then the load scale.
@@ -709,14 +705,13 @@ __device__ __forceinline__ void pair_inputs(const StepIO<T> &io, const Rows<kWal
 }
 
 // The collision of an in-place step, then the pair's reference (BF16).
-template <int Q, typename T, bool kEq>
+template <int Q, typename T, bool kEq, bool kForce>
 __device__ __forceinline__ float4 pair_collide(const StepIO<T> &io, const StepArgs &a,
                                                const PackedRates &pr, int x0, int y, int z,
                                                int own, f2 (&f)[Q]) {
-    f2 Fx, Fy, Fz, ux, uy, uz;
-    pair_force(a, x0, y, z, Fx, Fy, Fz);
-    PairCollide<Q>::template run<kFoldedLoad<Q, T>(), kEq>(f, Fx, Fy, Fz, pr, a.has_force != 0,
-                                                           ux, uy, uz);
+    f2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f), ux, uy, uz;
+    if constexpr (kForce) pair_force(a, x0, y, z, Fx, Fy, Fz);
+    PairCollide<Q>::template run<kFoldedLoad<Q, T>(), kEq, kForce>(f, Fx, Fy, Fz, pr, ux, uy, uz);
     float4 J = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if constexpr (Storage<T>::kRef) {
         J = pair_ref(ux, uy, uz);
@@ -725,7 +720,7 @@ __device__ __forceinline__ float4 pair_collide(const StepIO<T> &io, const StepAr
     return J;
 }
 
-template <int Q, typename T, bool kWalls, bool kEq>
+template <int Q, typename T, bool kWalls, bool kEq, bool kForce>
 __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const StepArgs a,
                                                       const PackedRates pr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -744,7 +739,7 @@ __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const 
     pair_inputs<Q, T, kWalls>(io, R, x0, xm, xp, f);
     unsigned seed = 0;
     if constexpr (!kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
-    const float4 J = pair_collide<Q, T, kEq>(io, a, pr, x0, y, z, own, f);
+    const float4 J = pair_collide<Q, T, kEq, kForce>(io, a, pr, x0, y, z, own, f);
     if constexpr (kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
@@ -755,12 +750,13 @@ __global__ void __launch_bounds__(128) aa_even_kernel(const StepIO<T> io, const 
 
 // Blocks of 128 per SM, from measurement: D3Q27 at 5 (96 registers; FP32
 // storage without spills, 16-bit with 40 bytes: 38.3k vs 33.3k MLUPS FP16 at
-// 512^3 against 3 blocks); D3Q15 at 4 (24-32 bytes of spills).
-template <int Q, typename T>
-constexpr int kAAOddBlocks = Q == 27 ? 5 : 4;
+// 512^3 against 3 blocks); D3Q15 with force at 4 (8-48 bytes of spills),
+// without force at 5 (no spills; FP16 77.7k vs 68.9k MLUPS at 256^3 against 4).
+template <int Q, typename T, bool kForce>
+constexpr int kAAOddBlocks = Q == 27 ? 5 : (kForce ? 4 : 5);
 
-template <int Q, typename T, bool kWalls, bool kEq>
-__global__ void __launch_bounds__(128, (kAAOddBlocks<Q, T>))
+template <int Q, typename T, bool kWalls, bool kEq, bool kForce>
+__global__ void __launch_bounds__(128, (kAAOddBlocks<Q, T, kForce>))
     aa_odd_kernel(const StepIO<T> io, const StepArgs a, const PackedRates pr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
@@ -792,7 +788,7 @@ __global__ void __launch_bounds__(128, (kAAOddBlocks<Q, T>))
     pair_inputs<Q, T, kWalls>(io, R, x0, xm, xp, f);
     unsigned seed = 0;
     if constexpr (!kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
-    const float4 J = pair_collide<Q, T, kEq>(io, a, pr, x0, y, z, own, f);
+    const float4 J = pair_collide<Q, T, kEq, kForce>(io, a, pr, x0, y, z, own, f);
     if constexpr (kSeedAfterCollision<Q, T>) seed = pair_seed<Q>(f, own);
     static_for<Q>([&](auto iq) {
         constexpr int q = decltype(iq)::value;
@@ -1060,10 +1056,14 @@ cudaError_t launch_step(const void *fin, void *fout, const StepArgs &a, cudaStre
             half.nx = a.g.nx / 2;
             const CellLaunch L = cell_launch(half);
             const PackedRates pr = packed_rates(a);
-            if (walls)
-                step2_q15_kernel<T, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+            if (walls && a.has_force)
+                step2_q15_kernel<T, true, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+            else if (walls)
+                step2_q15_kernel<T, true, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
+            else if (a.has_force)
+                step2_q15_kernel<T, false, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
             else
-                step2_q15_kernel<T, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
+                step2_q15_kernel<T, false, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
             return cudaGetLastError();
         }
     }
@@ -1077,8 +1077,23 @@ cudaError_t launch_step(const void *fin, void *fout, const StepArgs &a, cudaStre
     return cudaGetLastError();
 }
 
+template <int Q, typename T, bool kEq, bool kForce>
+void launch_aa_kernels(const StepIO<T> &io, const StepArgs &a, const PackedRates &pr, bool even,
+                       const CellLaunch &L, cudaStream_t st) {
+    if (even && a.g.bc)
+        aa_even_kernel<Q, T, true, kEq, kForce><<<L.grid, L.block, 0, st>>>(io, a, pr);
+    else if (even)
+        aa_even_kernel<Q, T, false, kEq, kForce><<<L.grid, L.block, 0, st>>>(io, a, pr);
+    else if (a.g.bc)
+        aa_odd_kernel<Q, T, true, kEq, kForce><<<L.grid, L.block, 0, st>>>(io, a, pr);
+    else
+        aa_odd_kernel<Q, T, false, kEq, kForce><<<L.grid, L.block, 0, st>>>(io, a, pr);
+}
+
 // One in-place (AA) step on buffer buf: even (kAANatural -> kAASwapped) or
-// odd (kAASwapped -> kAANatural).  nx must be even.
+// odd (kAASwapped -> kAANatural).  nx must be even.  D3Q27 takes the rate-1
+// form when omega_9..26 are all 1; D3Q15 the force-free cascade when there is
+// no force.
 template <int Q, typename T>
 cudaError_t launch_step_aa(void *buf, const StepArgs &a, bool even, cudaStream_t st) {
     StepIO<T> io;
@@ -1095,25 +1110,17 @@ cudaError_t launch_step_aa(void *buf, const StepArgs &a, bool even, cudaStream_t
     half.nx = a.g.nx / 2;
     const CellLaunch L = cell_launch(half);
     const PackedRates pr = packed_rates(a, kFoldedLoad<Q, T>());
-    if (Q == 27 && higher_rates_are_one(a)) {
-        if (even && a.g.bc)
-            aa_even_kernel<Q, T, true, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
-        else if (even)
-            aa_even_kernel<Q, T, false, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
-        else if (a.g.bc)
-            aa_odd_kernel<Q, T, true, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
+    if constexpr (Q == 27) {
+        if (higher_rates_are_one(a))
+            launch_aa_kernels<Q, T, true, true>(io, a, pr, even, L, st);
         else
-            aa_odd_kernel<Q, T, false, true><<<L.grid, L.block, 0, st>>>(io, a, pr);
-        return cudaGetLastError();
+            launch_aa_kernels<Q, T, false, true>(io, a, pr, even, L, st);
+    } else {
+        if (a.has_force)
+            launch_aa_kernels<Q, T, false, true>(io, a, pr, even, L, st);
+        else
+            launch_aa_kernels<Q, T, false, false>(io, a, pr, even, L, st);
     }
-    if (even && a.g.bc)
-        aa_even_kernel<Q, T, true, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
-    else if (even)
-        aa_even_kernel<Q, T, false, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
-    else if (a.g.bc)
-        aa_odd_kernel<Q, T, true, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
-    else
-        aa_odd_kernel<Q, T, false, false><<<L.grid, L.block, 0, st>>>(io, a, pr);
     return cudaGetLastError();
 }
 
