@@ -52,12 +52,14 @@ GRIDS = [(3, 4, 2), (7, 3, 6), (9, 10, 38), (2, 33, 64)]  # (nz, ny, nx), nx eve
 @pytest.mark.parametrize("Q", [27, 15])
 @pytest.mark.parametrize("bc", [0, 1, 2, 3])
 @pytest.mark.parametrize("shape", GRIDS)
-def test_inplace_equals_two_buffer_bitwise(lbm, Q, bc, shape):
-    """Random state, uniform force, random rates: after 1, 2, 3 and 6 steps
-    (both parities of the in-place layout) the states are identical."""
+@pytest.mark.parametrize("force", [(3e-3, -2e-3, 1e-3), (0.0, 0.0, 0.0)])
+def test_inplace_equals_two_buffer_bitwise(lbm, Q, bc, shape, force):
+    """Random state, uniform force (or zero: the D3Q15 force-free kernels),
+    random rates: after 1, 2, 3 and 6 steps (both parities of the in-place
+    layout) the states are identical."""
     f0 = W.random_field_state(shape, Q, seed=300 + bc, spread=0.5)
     om = W.random_omegas(Q, seed=6)
-    two, one = pair(lbm, Q, shape, om, walls=bc, force=(3e-3, -2e-3, 1e-3))
+    two, one = pair(lbm, Q, shape, om, walls=bc, force=force)
     two.set_state(f0)
     one.set_state(f0)
     done = 0
@@ -71,11 +73,12 @@ def test_inplace_equals_two_buffer_bitwise(lbm, Q, bc, shape):
 
 @pytest.mark.parametrize("Q", [27, 15])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
-def test_inplace_16bit_storage_equals_two_buffer(lbm, Q, storage):
+@pytest.mark.parametrize("force", [(1e-4, 0.0, -1e-4), (0.0, 0.0, 0.0)])
+def test_inplace_16bit_storage_equals_two_buffer(lbm, Q, storage, force):
     shape = (6, 9, 20)
     rho, u = W.taylor_green(shape, u0=0.05, noise=1e-2, seed=41)
     om = W.omegas(Q, 1 / 0.6)
-    two, one = pair(lbm, Q, shape, om, storage=storage, walls=3, force=(1e-4, 0.0, -1e-4))
+    two, one = pair(lbm, Q, shape, om, storage=storage, walls=3, force=force)
     two.init_equilibrium(rho, u)
     one.init_equilibrium(rho, u)
     for n in (1, 4):

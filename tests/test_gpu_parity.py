@@ -76,6 +76,22 @@ def test_one_step_from_random_state(lbm, orc, Q, bc, shape):
     assert np.abs(got - want).max() <= 2e-6
 
 
+@pytest.mark.parametrize("Q", [27, 15])
+@pytest.mark.parametrize("bc", [0, 3])
+@pytest.mark.parametrize("shape", GRIDS)
+def test_one_step_force_free_from_random_state(lbm, orc, Q, bc, shape):
+    """No force anywhere: the D3Q15 kernels then run the force-free cascade,
+    compiled on its own; element by element against the oracle."""
+    f0 = W.random_field_state(shape, Q, seed=110 + bc, spread=0.5)
+    om = W.random_omegas(Q, seed=7)
+    S = lbm.Solver(Q, shape, om, walls=bc)
+    S.set_state(f0)
+    S.step(1)
+    got = gpu_state(S)
+    want = orc.run(Q, shape, f0, np.zeros(3), om, 1, bc=bc)
+    assert np.abs(got - want).max() <= 2e-6
+
+
 DEGENERATE = [(1, 1, 1), (1, 1, 2), (2, 1, 6), (1, 5, 4), (3, 2, 1)]  # (nz, ny, nx)
 
 
@@ -289,25 +305,36 @@ def test_16bit_storage_taylor_green(lbm, orc, storage, bound):
 @pytest.mark.parametrize("Q", [27, 15])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("shape", [(6, 11, 35), (6, 11, 36)])  # one-cell and two-cell kernels
-def test_16bit_storage_walled_channel(lbm, orc, Q, storage, shape):
+@pytest.mark.parametrize("forced", [True, False])
+def test_16bit_storage_walled_channel(lbm, orc, Q, storage, shape, forced):
     """Both step kernels' stochastically rounded 16-bit stores (odd nx: one
-    cell per thread; even nx: pairs) on a walled channel with a force field:
-    velocity after 40 steps against the FP64 oracle, relative L2 within
-    1e-3."""
+    cell per thread; even nx: pairs) on a walled channel, with a force field
+    or no force at all (the D3Q15 force-free kernels): velocity after 40
+    steps against the FP64 oracle, relative L2 within 1e-3.  Without the
+    drive the velocity decays (about 3x over 40 steps in this narrow channel)
+    while the rounding noise does not, so that case is compared after 10.
+    D3Q15 with BF16 storage: within 2e-3, since its corner populations hold
+    1/3 of the momentum weight sum_a w_a e_a e_a and carry no momentum
+    reference (D3Q27's corners hold 1/9), which leaves about twice the
+    rounding noise (measured 7.5e-4 driven, 1.5e-3 decaying)."""
     om = W.omegas(Q, 1.25)
-    F = W.rng(15).uniform(-1e-4, 1e-4, (3,) + shape) + np.array([1e-4, 0, 0])[:, None, None,
-                                                                              None]
+    if forced:
+        F = W.rng(15).uniform(-1e-4, 1e-4, (3,) + shape) + np.array([1e-4, 0, 0])[:, None, None,
+                                                                                  None]
+    else:
+        F = np.zeros(3)
+    steps = 40 if forced else 10
     F32 = F.astype(np.float32).astype(np.float64)
     rho0, u0 = W.taylor_green(shape, u0=0.02, noise=1e-3)
     S = lbm.Solver(Q, shape, om, force=F, walls=3, storage=storage)
     S.init_equilibrium(rho0, u0)
-    S.step(40)
-    f_or = orc.run(Q, shape, orc.equilibrium(Q, rho0, u0, F32), F32, om, 40, bc=3)
+    S.step(steps)
+    f_or = orc.run(Q, shape, orc.equilibrium(Q, rho0, u0, F32), F32, om, steps, bc=3)
     _, u_g = orc.macroscopic(Q, gpu_state(S), F32)
     _, u_o = orc.macroscopic(Q, f_or, F32)
     err = rel_l2(u_g, u_o)
     print("D3Q%d %s %s: rel L2 u = %.3e" % (Q, storage, shape, err))
-    assert err <= 1e-3
+    assert err <= (2e-3 if (Q, storage) == (15, "bf16") else 1e-3)
 
 
 @pytest.fixture(scope="module")
