@@ -9,12 +9,13 @@
 // S = K D^-1 m^s the source of App. G.
 //
 // GB300 form: templated on the value type (float, or f2 = two neighbouring
-// cells in packed f32x2 arithmetic), and the update K.g + S is evaluated by
-// sign patterns instead of a 15 x 11 product: on the 8 corners
-// (sx, sy, sz) every basis vector is one of 1, sx, sy, sz, sx sy, sx sz,
-// sy sz, sx sy sz times a constant, so the 8 increments are a three-level
-// butterfly of 8 coefficients; each axis pair (+-x etc.) is an even part plus
-// or minus an odd part.
+// cells in packed f32x2 arithmetic), and both directions between the
+// populations and the moments go by sign patterns instead of 15 x 15 and
+// 15 x 11 products: on the 8 corners (sx, sy, sz) every basis vector and
+// every raw moment the cascade needs is one of 1, sx, sy, sz, sx sy, sx sz,
+// sy sz, sx sy sz times a constant, so the moment sums and the 8 corner
+// increments are three-level butterflies; each axis pair (+-x etc.) enters
+// as a sum and a difference (even and odd parts).
 //
 // Precision: the state is carried as deviations from the weights
 // (2/9, 1/9, 1/72).  The weights' raw moments are 1 (mass), 1/3 (xx, yy, zz)
