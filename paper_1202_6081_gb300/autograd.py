@@ -17,7 +17,9 @@ every ``every`` steps.  Backward: for each segment, last to first, the
 segment's states are recomputed from its checkpoint into a ring of buffers
 (``lbm_step_into``), then ``lbm_adjoint_step`` runs from the segment's last
 step back to its first, accumulating dJ/dF on the device; the final state
-seeds the adjoint (``lbm_kinetic_energy_seed``).  Every step runs in the CUDA
+seeds the adjoint (``lbm_kinetic_energy_seed``).  The recomputation of the
+next segment runs on a second stream, beside the adjoint steps of the
+current one.  Every step runs in the CUDA
 kernels of liblbm.so; torch holds the buffers.
 """
 from __future__ import annotations
@@ -76,25 +78,62 @@ def _forward_with_checkpoints(solver, nsteps, every):
 def _backward_segments(S, nsteps, every, ckpts, seed, gF):
     """Adjoint sweep over the checkpointed segments, last to first; `seed`
     fills the adjoint field from the final state.  Returns the adjoint of
-    the initial state (a pitched FP32 field)."""
+    the initial state (a pitched FP32 field).
+
+    Two rings of state buffers: while the adjoint steps of segment s run on
+    the caller's stream from one ring, a second stream recomputes the states
+    of segment s - 1 into the other, so the two memory-bound sweeps share
+    the GPU (events order each ring's reuse)."""
     lam = S.new_adjoint_field()
     lam2 = S.new_adjoint_field()
-    ring = [S.new_state_buffer() for _ in range(min(every, nsteps) + 1)]
+    m = min(every, nsteps) + 1
+    rings = [[S.new_state_buffer() for _ in range(m)] for _ in range(2)]
     nseg = len(ckpts)
-    for s in reversed(range(nseg)):
+    cuda = rings[0][0].is_cuda  # host-side fakes run the same schedule in order
+    if cuda:
+        dev = rings[0][0].device
+        main = torch.cuda.current_stream(dev)
+        side = torch.cuda.Stream(device=dev)
+        ready = [torch.cuda.Event(), torch.cuda.Event()]  # ring r holds its segment
+        free = [torch.cuda.Event(), torch.cuda.Event()]   # ring r may be overwritten
+        side.wait_stream(main)  # checkpoints, force field and buffers are ready
+
+    def bounds(s):
         t0 = s * every
-        t1 = min(t0 + every, nsteps)
-        ring[0].copy_(ckpts[s])
+        return t0, min(t0 + every, nsteps)
+
+    def recompute(s, ring):
         # the adjoint steps need the states t0 .. t1 - 1; the state at t1 is
         # recomputed only in the last segment, where it seeds the adjoint
-        last = s == nseg - 1
-        for i in range(t1 - t0 if last else t1 - t0 - 1):
+        t0, t1 = bounds(s)
+        ring[0].copy_(ckpts[s])
+        for i in range(t1 - t0 if s == nseg - 1 else t1 - t0 - 1):
             S.step_into(ring[i], ring[i + 1])
-        if last:
+
+    recompute(nseg - 1, rings[0])
+    r = 0
+    for s in reversed(range(nseg)):
+        if s > 0:
+            if cuda:
+                with torch.cuda.stream(side):
+                    if s < nseg - 1:
+                        side.wait_event(free[1 - r])  # its last adjoint sweep is done
+                    recompute(s - 1, rings[1 - r])
+                    ready[1 - r].record(side)
+            else:
+                recompute(s - 1, rings[1 - r])
+        t0, t1 = bounds(s)
+        ring = rings[r]
+        if s == nseg - 1:
             seed(ring[t1 - t0], lam)
         for i in reversed(range(t1 - t0)):
             S.adjoint_step(ring[i], lam, lam2, gF)
             lam, lam2 = lam2, lam
+        if cuda:
+            free[r].record(main)
+            if s > 0:
+                main.wait_event(ready[1 - r])
+        r = 1 - r
     return lam
 
 
