@@ -75,21 +75,39 @@ def _forward_with_checkpoints(solver, nsteps, every):
     return ckpts
 
 
+def _second_ring_fits(ring):
+    """Whether a second ring like `ring` fits in the device memory still free
+    (the driver's free memory plus the blocks torch holds cached), with 1 GiB
+    to spare.  Host tensors (test fakes): always."""
+    if not ring[0].is_cuda:
+        return True
+    dev = ring[0].device
+    free, _ = torch.cuda.mem_get_info(dev)
+    cached = torch.cuda.memory_reserved(dev) - torch.cuda.memory_allocated(dev)
+    need = sum(b.numel() * b.element_size() for b in ring)
+    return free + cached >= need + (1 << 30)
+
+
 def _backward_segments(S, nsteps, every, ckpts, seed, gF):
     """Adjoint sweep over the checkpointed segments, last to first; `seed`
     fills the adjoint field from the final state.  Returns the adjoint of
     the initial state (a pitched FP32 field).
 
-    Two rings of state buffers: while the adjoint steps of segment s run on
-    the caller's stream from one ring, a second stream recomputes the states
-    of segment s - 1 into the other, so the two memory-bound sweeps share
-    the GPU (events order each ring's reuse)."""
+    Two rings of state buffers when they fit: while the adjoint steps of
+    segment s run on the caller's stream from one ring, a second stream
+    recomputes the states of segment s - 1 into the other, so the two
+    memory-bound sweeps share the GPU (events order each ring's reuse).
+    Otherwise one ring, each segment recomputed after the adjoint steps of
+    the one after it."""
     lam = S.new_adjoint_field()
     lam2 = S.new_adjoint_field()
     m = min(every, nsteps) + 1
-    rings = [[S.new_state_buffer() for _ in range(m)] for _ in range(2)]
     nseg = len(ckpts)
-    cuda = rings[0][0].is_cuda  # host-side fakes run the same schedule in order
+    rings = [[S.new_state_buffer() for _ in range(m)]]
+    two = nseg > 1 and _second_ring_fits(rings[0])
+    if two:
+        rings.append([S.new_state_buffer() for _ in range(m)])
+    cuda = two and rings[0][0].is_cuda  # host-side fakes run the same schedule in order
     if cuda:
         dev = rings[0][0].device
         main = torch.cuda.current_stream(dev)
@@ -113,7 +131,7 @@ def _backward_segments(S, nsteps, every, ckpts, seed, gF):
     recompute(nseg - 1, rings[0])
     r = 0
     for s in reversed(range(nseg)):
-        if s > 0:
+        if two and s > 0:
             if cuda:
                 with torch.cuda.stream(side):
                     if s < nseg - 1:
@@ -129,6 +147,10 @@ def _backward_segments(S, nsteps, every, ckpts, seed, gF):
         for i in reversed(range(t1 - t0)):
             S.adjoint_step(ring[i], lam, lam2, gF)
             lam, lam2 = lam2, lam
+        if not two:
+            if s > 0:
+                recompute(s - 1, rings[0])
+            continue
         if cuda:
             free[r].record(main)
             if s > 0:

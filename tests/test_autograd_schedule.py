@@ -47,7 +47,11 @@ class FakeSolver:
 
 @pytest.mark.parametrize("nsteps,every", [(30, 7), (28, 7), (20, 20), (21, 20), (5, 8), (1, 1),
                                           (1, 3), (9, 1)])
-def test_checkpoints_and_adjoint_order(nsteps, every):
+@pytest.mark.parametrize("two_rings", [True, False])
+def test_checkpoints_and_adjoint_order(monkeypatch, nsteps, every, two_rings):
+    """Both schedules: two rings (the next segment recomputed beside the
+    current one's adjoint steps) and one ring (when a second does not fit)."""
+    monkeypatch.setattr(AG, "_second_ring_fits", lambda ring: two_rings)
     S = FakeSolver()
     ckpts = AG._forward_with_checkpoints(S, nsteps, every)
     # forward: one step() call per segment, a checkpoint at every segment start
